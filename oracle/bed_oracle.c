@@ -348,19 +348,23 @@ void orc_secular_root(int K, const double* d, const double* z, double rho, doubl
 
 /*
  * Eq. (25): z-hat_i = sqrt( prod_j (lambda_j - d_i) / (rho prod_{j != i} (d_j - d_i)) ),
- * given the roots as (origin, tau) pairs over the same poles; the sign is taken
+ * given the roots as (origin, tau) pairs over the same DESCENDING poles; the sign is taken
  * from z_i. lambda_j - d_i is formed as (d_{o_j} - d_i) + tau_j.
+ * The two products of Eq. (25) under- or overflow once many poles cluster (K factors of size
+ * 1e-9 already underflow binary64), so the same quotient is evaluated as the product of
+ * interlaced ratios, each in (0, 1) by Eq. (9):
+ *   (lambda_0 - d_i)/rho * prod_{j<i} (lambda_{j+1} - d_i)/(d_j - d_i)
+ *                        * prod_{j>i} (lambda_j - d_i)/(d_j - d_i),
+ * starting with the one factor that may exceed 1, so no partial product leaves the range
+ * of the result.
  */
 void orc_loewner_zhat(int K, const double* d, const double* z, double rho, const int* origin,
                       const double* tau, double* zhat)
 {
     for (int i = 0; i < K; i++) {
-        double num = 1.0, den = rho;
-        for (int j = 0; j < K; j++) {
-            num *= (d[origin[j]] - d[i]) + tau[j];
-            if (j != i) den *= d[j] - d[i];
-        }
-        double q = num / den;
+        double q = ((d[origin[0]] - d[i]) + tau[0]) / rho;
+        for (int j = 0; j < i; j++) q *= ((d[origin[j + 1]] - d[i]) + tau[j + 1]) / (d[j] - d[i]);
+        for (int j = i + 1; j < K; j++) q *= ((d[origin[j]] - d[i]) + tau[j]) / (d[j] - d[i]);
         zhat[i] = (z[i] >= 0 ? 1.0 : -1.0) * sqrt(q > 0 ? q : 0.0);
     }
 }

@@ -30,7 +30,9 @@ MUTATIONS = {
     "section_update_swapped": ("        it++;\n        ns++;\n        if (f > 0)\n            U = h;\n        else if (f < 0)\n            L = h;",
                                "        it++;\n        ns++;\n        if (f < 0)\n            U = h;\n        else if (f > 0)\n            L = h;"),
     "zhat_sign_dropped": ("zhat[i] = (z[i] >= 0 ? 1.0 : -1.0) * sqrt(q > 0 ? q : 0.0);", "zhat[i] = sqrt(q > 0 ? q : 0.0);"),
-    "zhat_denominator_index": ("if (j != i) den *= d[j] - d[i];", "if (j != i) den *= d[j] - d[0] + 1.0;"),
+    "zhat_ratio_index": ("for (int j = 0; j < i; j++) q *= ((d[origin[j + 1]] - d[i]) + tau[j + 1]) / (d[j] - d[i]);",
+                         "for (int j = 0; j < i; j++) q *= ((d[origin[j]] - d[i]) + tau[j]) / (d[j] - d[i]);"),
+    "zhat_drops_rho": ("double q = ((d[origin[0]] - d[i]) + tau[0]) / rho;", "double q = ((d[origin[0]] - d[i]) + tau[0]);"),
     "vector_shift_sign": ("double q = zh[i] / ((dK[i] - dK[orig[j]]) - tau[j]);", "double q = zh[i] / ((dK[i] - dK[orig[j]]) + tau[j]);"),
     "rotation_undo_sign": ("Y[q * s + k] = -sn * yp + c * yq;", "Y[q * s + k] = sn * yp + c * yq;"),
     "rotation_new_pole": ("dd[p] = sn * sn * a + c * c * b;", "dd[p] = c * c * a + sn * sn * b;"),

@@ -247,6 +247,25 @@ def test_loewner_zhat_with_exact_roots_recovers_z(K):
     assert np.allclose(zh, z, rtol=1e-8, atol=0)
 
 
+def test_loewner_zhat_clustered_poles():
+    """Eq. (25) when 56 poles cluster at the 1e-9 scale: the two plain products of Eq. (25) underflow
+    binary64 (56 factors of ~1e-9), the quotient does not; |z^| must still equal |z| with exact roots."""
+    rng = np.random.default_rng(210)
+    K = 56
+    d = np.sort(rng.uniform(-1e-9, 5e-9, K))[::-1].copy()
+    z = rng.standard_normal(K)
+    z /= np.linalg.norm(z) / np.sqrt(2.0)
+    rho = 1e-9
+    lam = np.linalg.eigvalsh(np.diag(d) + rho * np.outer(z, z))[::-1]
+    o = np.empty(K, np.int32)
+    for i in range(K):
+        cands = [i] + ([i - 1] if i > 0 else [])
+        o[i] = min(cands, key=lambda j: abs(lam[i] - d[j]))
+    zh = oracle.loewner_zhat(d, z, rho, o, lam - d[o])
+    assert np.all(np.isfinite(zh))
+    assert np.allclose(zh, z, rtol=1e-6, atol=0)
+
+
 # ----------------------------------------------------------------------------- a4-a6: one merge
 
 
@@ -407,11 +426,13 @@ def test_whole_path_diagonal_and_sign_convention():
     assert np.all(V[idx, np.arange(12)] > 0)
 
 
+@pytest.mark.parametrize("n", [16, 64])
 @pytest.mark.parametrize("name", ["zero", "identity", "diagonal", "repeated", "rank_one", "block_diagonal", "toeplitz"])
-def test_whole_path_special_cases(name):
-    M = wl.special_cases(16)[name].astype(np.float64)
-    W, V, _ = oracle.eigh(M)
-    _check_eigpairs(M, W, V, 1e-13 * 16)
+def test_whole_path_special_cases(name, n):
+    M = wl.special_cases(n)[name].astype(np.float64)
+    W, V, st = oracle.eigh(M)
+    _check_eigpairs(M, W, V, 1e-13 * n)
+    assert st.not_conv == 0
 
 
 def test_batch_driver_matches_single_and_is_thread_independent():
