@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Throughput of the batched divide-and-conquer symmetric eigensolver on one GB300 (or N, weak scaling).
+
+Workload (one step): the uniform-size covariance batches -- 512 FP32 matrices A = X X^T/m + 1e-3 I
+(X an n x 2n seeded N(0,1) matrix) at each n in {16, 32, 48, 64}, i.e. 2048 eigendecompositions per
+step, one launch per n on one stream. Metric: matrices/s at the stated error (the GPU tests hold every
+config to the oracle within tolerance).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: W untimed steps, then exactly K steps, each bracketed by CUDA events on the launching stream;
+the L2 is flushed (a 512 MB write) before every step, outside the events. Barrier + synchronize on both
+sides of the timed region, max over ranks. The end-to-end number runs the same workload through the
+public API from pinned host memory (host->device copy, kernels, device->host copy of W, V and info)
+with a wall clock. ``--impl reference`` times the FP64 oracle (a deliberately plain CPU program) on the
+host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SIZES = (16, 32, 48, 64)
+BATCH = 512
+METRIC = "matrices/s for batched n<=64 FP32 ED at stated error"
+WORKLOAD = "uniform covariance batches: 512 x n in {16,32,48,64}, FP32 A = XX^T/2n + 1e-3 I"
+L2_FLUSH_BYTES = 512 << 20
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_eigh_n64_b512.txt")
+KERNEL_SOURCES = ["paper_2604_27325_gb300/csrc/bed_kernel.cuh", "paper_2604_27325_gb300/csrc/bed_api.cu",
+                  "paper_2604_27325_gb300/csrc/bed_internal.h"]
+
+
+def flops_per_matrix(n: int, kbar: float) -> float:
+    """Algorithmic FP32 FLOPs per matrix: (4/3)n^3 tridiagonalization + (4/3)n^3 merge GEMMs +
+    2n^3 back-transform + 16 kbar n^2 secular evaluations + 18 n^2 eigenvector formation."""
+    return (14.0 / 3.0) * n**3 + (16.0 * kbar + 18.0) * n**2
+
+
+def bytes_per_matrix(n: int) -> int:
+    """Algorithmic HBM bytes per matrix: read A, write V and W."""
+    return 4 * (2 * n * n + n)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic():
+    """DRAM bytes per n=64 launch from the committed ncu summary, if taken on the current kernel."""
+    try:
+        kv = dict(l.split("=", 1) for l in open(TRAFFIC_FILE).read().split("\n") if "=" in l)
+        if kv.get("kernel_source_sha", "").strip() == kernel_source_hash():
+            return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled every 50 ms in the background."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                    rows.append({"t": ts, "sm": float(parts[2]), "max": float(parts[3]),
+                                 "hw": parts[6], "hwt": parts[7], "swt": parts[8], "pcap": parts[9]})
+                except (ValueError, IndexError):
+                    continue
+        finally:
+            os.unlink(self.path)
+        return rows
+
+    @staticmethod
+    def summarize(rows, t0, t1):
+        inside = [r for r in rows if t0 <= r["t"] <= t1]
+        window = "timed region"
+        if len(inside) < 3:
+            inside = [r for r in rows if t0 - 2.0 <= r["t"] <= t1 + 0.5]
+            window = "timed region and the warm-up steps before it (timed region shorter than the sampling period)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "window": "no samples"}
+        reasons = set()
+        for r in inside:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in inside), "sm_max_mhz": max(r["max"] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
+
+
+# ------------------------------------------------------------------------------------------------ ranks
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        # host-side barrier and max-reduce of the timings only; the path itself has no exchange step
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(total: int, rank: int, world: int):
+    """Contiguous share of `total` independent units for `rank` (used by the multi-rank tests)."""
+    lo = total * rank // world
+    hi = total * (rank + 1) // world
+    return lo, hi
+
+
+# ------------------------------------------------------------------------------------------------ CPU legs
+
+
+def cpu_oracle_rate(inputs, budget_s: float, min_reps: int = 1):
+    """The FP64 oracle as it stands, on all host cores, over whole passes of the workload until
+    `budget_s` of wall time is spent. Returns (matrices/s, threads used, matrices solved)."""
+    import oracle
+
+    nthreads = os.cpu_count() or 1
+    used = 1
+    done = 0
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        for n in sorted(inputs):
+            _, _, _, used = oracle.eigh_batch_f32(inputs[n], nthreads=nthreads)
+            done += inputs[n].shape[0]
+        reps += 1
+        if reps >= min_reps and time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, used, done
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return 0
+    from paper_2604_27325_gb300 import workloads
+
+    # each step solves a bounded sample of the workload: 64 matrices of each size
+    sample = {n: workloads.covariance(BATCH, n)[:64] for n in SIZES}
+    per_step = sum(a.shape[0] for a in sample.values())
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sample, 0.0)
+    t0 = time.perf_counter()
+    used = 1
+    for _ in range(args.steps):
+        _, used, _ = cpu_oracle_rate(sample, 0.0)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded covariance matrices)",
+        "config": {"workload": WORKLOAD, "batch": BATCH, "sizes": list(SIZES),
+                   "sample_per_step": "64 of the 512 matrices at each n (256 per step)"},
+        "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": used, "kind": "oracle",
+                         "sample": "64 matrices at each n in {16,32,48,64} per step"},
+        "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------ GPU arm
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2604_27325_gb300 import binding as B
+    from paper_2604_27325_gb300 import workloads
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.lib()
+    props = torch.cuda.get_device_properties(dev)
+    inputs = {n: workloads.covariance(BATCH, n) for n in SIZES}
+    Ad = {n: torch.from_numpy(a).to(dev) for n, a in inputs.items()}
+    Wd = {n: torch.empty(BATCH, n, device=dev) for n in SIZES}
+    Vd = {n: torch.empty(BATCH, n, n, device=dev) for n in SIZES}
+    Id = {n: torch.empty(BATCH, dtype=torch.int32, device=dev) for n in SIZES}
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def launch(n):
+        st = B.bed_eigh_f32(Ad[n].data_ptr(), Wd[n].data_ptr(), Vd[n].data_ptr(), Id[n].data_ptr(), BATCH, n,
+                            None, sp)
+        if st != B.BED_OK:
+            raise B.BedError(B.bed_status_string(st) + " " + B.bed_last_cuda_error())
+
+    # secular-iteration counts for the FLOP model (one counted pass, outside the timing)
+    kbar = {}
+    for n in SIZES:
+        cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+        st = B.bed_eigh_f32_counted(Ad[n].data_ptr(), Wd[n].data_ptr(), Vd[n].data_ptr(), Id[n].data_ptr(),
+                                    BATCH, n, None, cnt.data_ptr(), sp)
+        assert st == B.BED_OK
+        c = cnt.tolist()
+        kbar[n] = c[2] / max(c[1], 1)
+    torch.cuda.synchronize(dev)
+    bad = sum(int((Id[n] != 0).sum()) for n in SIZES)
+    if bad:
+        raise RuntimeError(f"{bad} matrices reported a non-zero info")
+
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        for n in SIZES:
+            launch(n)
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(SIZES) + 1)] for _ in range(K)]
+    sampler = ClockSampler(local).start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t_start = time.time()
+    for s in range(K):
+        flush.fill_(float(s))  # > L2: every step starts cold
+        ev[s][0].record(stream)
+        for j, n in enumerate(SIZES):
+            launch(n)
+            ev[s][j + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    t_end = time.time()
+    barrier(world)
+    rows = sampler.stop()
+    clocks = ClockSampler.summarize(rows, t_start, t_end)
+
+    step_ms = [ev[s][0].elapsed_time(ev[s][-1]) for s in range(K)]
+    per_n_ms = {n: [ev[s][j].elapsed_time(ev[s][j + 1]) for s in range(K)] for j, n in enumerate(SIZES)}
+    total_ms = max_over_ranks(sum(step_ms), world)
+    ms_per_step = total_ms / K
+    per_step_units = BATCH * len(SIZES)
+    value = per_step_units * world * K / (total_ms / 1e3)
+
+    # roofline of the dominant launch (n = 64)
+    peaks = measured_peaks()
+    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz_max * 1e6 / 1e12  # TFLOP/s
+    dom = max(SIZES, key=lambda n: statistics.mean(per_n_ms[n]))
+    t_dom = statistics.mean(per_n_ms[dom]) / 1e3
+    achieved = flops_per_matrix(dom, kbar[dom]) * BATCH / t_dom / 1e12
+    traffic = read_traffic() if dom == 64 else None
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm = bytes_per_matrix(dom) * BATCH / t_dom / 1e9
+
+    # end to end through the public API with host buffers
+    host = {n: torch.from_numpy(inputs[n]).pin_memory() for n in SIZES}
+    for _ in range(max(1, min(args.warmup, 3))):
+        for n in SIZES:
+            B.batched_eigh(host[n])
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        for n in SIZES:
+            B.batched_eigh(host[n])
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    barrier(world)
+    h2d = sum(4 * BATCH * n * n for n in SIZES)
+    d2h = sum(4 * BATCH * (n * n + n) + 4 * BATCH for n in SIZES)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded covariance matrices, FP32)",
+        "config": {"workload": WORKLOAD, "batch": BATCH, "sizes": list(SIZES), "matrices_per_step": per_step_units,
+                   "launch": "one launch per n on one stream", "parallelism": f"dp{world} (independent matrices)",
+                   "l2": "flushed before every step (512 MB write), flush outside the per-step CUDA events"},
+        "per_n_ms": {str(n): statistics.mean(v) for n, v in per_n_ms.items()},
+        "kbar": {str(n): kbar[n] for n in SIZES},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": traffic,
+                     "kernel": f"eigh_kernel n={dom} batch={BATCH}",
+                     "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_mhz_max:.0f} MHz",
+                     "hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm / hbm_peak,
+                             "frac_of_8tbs": hbm / 8000.0}},
+        "e2e": {"value": per_step_units * world * K / e2e_s, "unit": "matrices/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": K * len(SIZES),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, used, done = cpu_oracle_rate(inputs, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": rate, "unit": "matrices/s", "cores": used, "kind": "oracle",
+                                "sample": f"whole passes of the workload ({done} matrices, about "
+                                          f"{args.cpu_budget:.0f} s wall on {used} threads)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=5.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

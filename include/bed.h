@@ -1,0 +1,130 @@
+/*
+ * bed.h -- C ABI of the batched divide-and-conquer symmetric eigensolver for mini-batches of small
+ * FP32 matrices (1 <= n <= 64) on NVIDIA GB300 (sm_103a).
+ *
+ * Method: Y. Song, "A Short Note on Batch-efficient Divide-and-Conquer Algorithm for
+ * EigenDecomposition" (arXiv 2604.27325), Sec. 2. Each matrix is reduced to tridiagonal form by
+ * Householder reflections (Sec. 2 defers this stage to the authors' earlier work), torn into
+ * rank-one-coupled blocks (Sec. 2.1, Eq. (1)-(3)) down to 2x2 leaves (Sec. 2.2), merged back through
+ * the secular equation (Sec. 2.3, Eq. (4)-(22)) with Gu-Eisenstat eigenvectors (Eq. (23)-(25)), and
+ * back-transformed. One launch runs the whole path for every matrix of the batch; each matrix lives
+ * in one thread block's shared memory.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are dense, row-major, contiguous FP32: A[b][i][j] at A + (b*n + i)*n + j.
+ *   - Only the lower triangle (i >= j) of A is read (the upper triangle may hold anything).
+ *   - W[b][j] (b*n + j) receives the eigenvalues in ascending order; V[b][i][j] receives component i
+ *     of the eigenvector of W[b][j] (eigenvectors are the COLUMNS of V[b]), so that
+ *     A[b] = V[b] diag(W[b]) V[b]^T. Each eigenvector is scaled to unit length and signed so that
+ *     its entry of largest magnitude (first such index on ties) is positive.
+ *   - info[b] receives a bit set of BED_INFO_* flags (0 = success); info may be NULL.
+ *   - All data pointers are DEVICE pointers owned by the caller; the library allocates no device
+ *     memory per call, never synchronizes, and returns as soon as the work is enqueued on `stream`
+ *     (0 = the legacy default stream). Results are ready when `stream` reaches that point.
+ *   - Argument errors are returned before anything is enqueued. A launch failure returns
+ *     BED_ERR_CUDA (the CUDA error string is available through bed_last_cuda_error()).
+ *   - Numerical outcomes never fail the call: they are reported per matrix through info.
+ */
+#ifndef BED_H
+#define BED_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BED_OK = 0,
+    BED_ERR_INVALID_ARG = 1,   /* null pointer, negative batch, misaligned pointer, bad params */
+    BED_ERR_UNSUPPORTED_N = 2, /* n outside [1, bed_max_n()] */
+    BED_ERR_CUDA = 3           /* the CUDA runtime refused the launch or an attribute call */
+} bed_status;
+
+/* per-matrix outcome flags written to info[b] */
+enum {
+    BED_INFO_OK = 0,
+    BED_INFO_NOT_CONVERGED = 1, /* a secular root hit the iteration cap; its last iterate is kept */
+    BED_INFO_NONFINITE = 2,     /* A[b] held a NaN or an infinity: W[b] and V[b] are set to NaN */
+    BED_INFO_TIMEOUT = 4        /* the staging copy of A[b] did not complete in time: W[b], V[b] NaN */
+};
+
+/*
+ * Constants of the method. The paper leaves all of them unnamed; bed_default_params() gives the
+ * defaults below. Passing NULL wherever a `const bed_params*` is taken means the defaults.
+ */
+typedef struct {
+    int leaf_size;           /* divide (Sec. 2.1) until blocks have <= leaf_size rows: 1 or 2 (default 2) */
+    int k_multisection;      /* k of Eq. (16), >= 2 (default 4) */
+    int max_section_iters;   /* cap on multi-section steps per root, 0..256 (default 24) */
+    int max_halley_iters;    /* cap on Halley steps per root, 1..256 (default 32) */
+    float section_rel_eps;   /* Eq. (17): sectioning stops when U - L < eps * (initial bracket), (0,1) (default 2^-6) */
+    float stop_c;            /* Halley stops when |f| <= stop_c * u * (1 + rho sum|z^2/(d - lambda)|), u = 2^-24 (default 8) */
+    float deflation_tol_scale; /* deflation tolerance = scale * u * max(max|d|, rho |z|^2) (default 8) */
+    int threads_per_matrix;  /* 0 = automatic; otherwise 2*nmax or 4*nmax threads, nmax in {16, 32, 64} the
+                                smallest that holds n */
+    int retire_by_vote;      /* 1 (default): a warp stops iterating secular roots as soon as all of its lanes
+                                have converged (the recast of the paper's progressive batch shrinkage,
+                                Eq. (22)); 0: every warp runs to the iteration caps with converged lanes
+                                idle. Results are bitwise identical either way. */
+} bed_params;
+
+/* Fills *p with the defaults listed above. */
+void bed_default_params(bed_params* p);
+
+/*
+ * Eigendecomposition of `batch` symmetric n x n FP32 matrices (Sec. 2, whole path).
+ *   A     [batch][n][n] device, read-only, 4-byte aligned (16-byte alignment and even n enable the
+ *         bulk-copy staging path).
+ *   W     [batch][n]    device, written.
+ *   V     [batch][n][n] device, written (may not alias A).
+ *   info  [batch]       device int32, written; may be NULL.
+ *   batch >= 0 (0: nothing is enqueued, BED_OK).
+ *   n     in [1, bed_max_n()].
+ *   p     NULL or parameters (validated; BED_ERR_INVALID_ARG if out of range).
+ *   stream CUDA stream to enqueue on.
+ */
+bed_status bed_eigh_f32(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
+                        const bed_params* p, cudaStream_t stream);
+
+/* Work counters a launch can accumulate (device memory, caller-owned, caller-zeroed). */
+typedef struct {
+    unsigned long long matrices;  /* matrices solved */
+    unsigned long long roots;     /* secular roots solved (non-deflated eigenvalues of all merges) */
+    unsigned long long evals;     /* evaluations of f (Eq. (8)) spent on those roots */
+    unsigned long long deflated;  /* eigenpairs deflated in merges */
+} bed_counters;
+
+/*
+ * Same as bed_eigh_f32, and additionally adds this launch's work counts to *counters (a DEVICE
+ * pointer to one bed_counters, updated with atomics; may not be NULL). Used to measure the mean
+ * number of secular iterations that enters the FLOP count.
+ */
+bed_status bed_eigh_f32_counted(const float* A, float* W, float* V, int32_t* info, int64_t batch,
+                                int n, const bed_params* p, bed_counters* counters,
+                                cudaStream_t stream);
+
+/* Largest supported n (64). */
+int bed_max_n(void);
+
+/* Static string naming a status code. */
+const char* bed_status_string(bed_status s);
+
+/* Text of the last CUDA error seen by a failing call on this thread ("" if none). */
+const char* bed_last_cuda_error(void);
+
+/*
+ * Host-side description of the divide tree the kernels follow for size n (Sec. 2.1: split at
+ * floor(s/2) until blocks have <= leaf_size rows). Pure host logic, no CUDA call.
+ *   merges  [3*64] receives (lo, mid, hi) of each merge, deepest level first (may be NULL)
+ *   level_of[64]   receives the merge level (0 = deepest) of each merge (may be NULL)
+ * Returns the number of merges (n - number of leaves), or -1 for an unsupported n / leaf_size.
+ */
+int bed_plan_describe(int n, int leaf_size, int* merges, int* level_of);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BED_H */

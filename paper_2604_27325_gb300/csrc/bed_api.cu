@@ -1,0 +1,213 @@
+// C ABI of the batched eigensolver: argument validation, the divide-tree plan, launch selection.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "bed_internal.h"
+
+namespace bed {
+
+namespace {
+
+struct MergeRec {
+    int lo, mid, hi, depth;
+};
+
+// Sec. 2.1: blocks are torn at floor(s/2) until they have at most leaf_size rows.
+void split(int lo, int hi, int depth, int leaf, std::vector<MergeRec>& merges, std::vector<int>& leaves)
+{
+    const int s = hi - lo;
+    if (s <= leaf) {
+        leaves.push_back(lo);
+        leaves.push_back(hi);
+        return;
+    }
+    const int mid = lo + s / 2;
+    split(lo, mid, depth + 1, leaf, merges, leaves);
+    split(mid, hi, depth + 1, leaf, merges, leaves);
+    merges.push_back({lo, mid, hi, depth});
+}
+
+thread_local char g_last_cuda_error[256] = "";
+
+bed_status cuda_fail(cudaError_t e)
+{
+    std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s: %s", cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+    return BED_ERR_CUDA;
+}
+
+}  // namespace
+
+bool build_plan(int n, int leaf_size, Plan* P)
+{
+    if (n < 1 || n > kMaxN || (leaf_size != 1 && leaf_size != 2)) return false;
+    std::vector<MergeRec> merges;
+    std::vector<int> leaves;
+    split(0, n, 0, leaf_size, merges, leaves);
+    std::memset(P, 0, sizeof *P);
+    P->n = n;
+    P->nleaves = static_cast<int>(leaves.size() / 2);
+    P->nmerge = static_cast<int>(merges.size());
+    for (int i = 0; i < P->nleaves; ++i) {
+        P->leaf_lo[i] = static_cast<uint8_t>(leaves[2 * i]);
+        P->leaf_hi[i] = static_cast<uint8_t>(leaves[2 * i + 1]);
+    }
+    int maxd = -1;
+    for (const auto& m : merges) maxd = m.depth > maxd ? m.depth : maxd;
+    P->nlevels = maxd + 1;
+    if (P->nlevels > kMaxLevels) return false;
+    std::memset(P->blk, 0xFF, sizeof P->blk);
+    int idx = 0;
+    for (int L = 0; L < P->nlevels; ++L) {  // level 0 = deepest merges
+        const int depth = maxd - L;
+        P->level_start[L] = static_cast<uint8_t>(idx);
+        for (const auto& m : merges) {
+            if (m.depth != depth) continue;
+            P->m_lo[idx] = static_cast<uint8_t>(m.lo);
+            P->m_mid[idx] = static_cast<uint8_t>(m.mid);
+            P->m_hi[idx] = static_cast<uint8_t>(m.hi);
+            for (int t = m.lo; t < m.hi; ++t) P->blk[L][t] = static_cast<uint8_t>(idx);
+            P->cut_mask |= 1ull << (m.mid - 1);
+            ++idx;
+        }
+    }
+    P->level_start[P->nlevels] = static_cast<uint8_t>(idx);
+    return true;
+}
+
+cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int32_t* info,
+                        int64_t batch, const Plan& P, const KParams& kp, bed_counters* counters,
+                        bool bulk, cudaStream_t stream)
+{
+#define BED_CASE(NM, GG)                                                                             \
+    if (nmax == NM && g == GG)                                                                       \
+        return launch_eigh_t<NM, GG>(A, W, V, info, batch, P, kp, counters, bulk, stream);
+    BED_CASE(16, 2)
+    BED_CASE(16, 4)
+    BED_CASE(32, 2)
+    BED_CASE(32, 4)
+    BED_CASE(64, 2)
+    BED_CASE(64, 4)
+#undef BED_CASE
+    return cudaErrorInvalidValue;
+}
+
+namespace {
+
+bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
+                       const bed_params* p, bed_counters* counters, cudaStream_t stream)
+{
+    if (n < 1 || n > kMaxN) return BED_ERR_UNSUPPORTED_N;
+    if (batch < 0) return BED_ERR_INVALID_ARG;
+    bed_params prm;
+    bed_default_params(&prm);
+    if (p) prm = *p;
+    if (prm.leaf_size != 1 && prm.leaf_size != 2) return BED_ERR_INVALID_ARG;
+    if (prm.k_multisection < 2 || prm.k_multisection > 64) return BED_ERR_INVALID_ARG;
+    if (prm.max_section_iters < 0 || prm.max_section_iters > 256) return BED_ERR_INVALID_ARG;
+    if (prm.max_halley_iters < 1 || prm.max_halley_iters > 256) return BED_ERR_INVALID_ARG;
+    if (!(prm.section_rel_eps > 0.f && prm.section_rel_eps < 1.f)) return BED_ERR_INVALID_ARG;
+    if (!(prm.stop_c >= 1.f && prm.stop_c <= 1e6f)) return BED_ERR_INVALID_ARG;
+    if (!(prm.deflation_tol_scale >= 1.f && prm.deflation_tol_scale <= 1e6f)) return BED_ERR_INVALID_ARG;
+    if (prm.retire_by_vote != 0 && prm.retire_by_vote != 1) return BED_ERR_INVALID_ARG;
+    const int nmax = n <= 16 ? 16 : (n <= 32 ? 32 : 64);
+    int g = 4;
+    if (prm.threads_per_matrix != 0) {
+        if (prm.threads_per_matrix == 2 * nmax) g = 2;
+        else if (prm.threads_per_matrix == 4 * nmax) g = 4;
+        else return BED_ERR_INVALID_ARG;
+    }
+    if (batch == 0) return BED_OK;
+    if (!A || !W || !V) return BED_ERR_INVALID_ARG;
+    const uintptr_t mis = (reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(W) |
+                           reinterpret_cast<uintptr_t>(V)) & 3u;
+    if (mis || (reinterpret_cast<uintptr_t>(info) & 3u) || (reinterpret_cast<uintptr_t>(counters) & 7u))
+        return BED_ERR_INVALID_ARG;
+    if (A == V) return BED_ERR_INVALID_ARG;
+    Plan P;
+    if (!build_plan(n, prm.leaf_size, &P)) return BED_ERR_INVALID_ARG;
+    KParams kp;
+    kp.k_ms = prm.k_multisection;
+    kp.max_sec = prm.max_section_iters;
+    kp.max_halley = prm.max_halley_iters;
+    kp.sec_eps = prm.section_rel_eps;
+    kp.stop_c = prm.stop_c;
+    kp.defl_c = prm.deflation_tol_scale;
+    kp.retire = prm.retire_by_vote;
+    // TMA bulk staging needs a 16-byte aligned source and a size that is a multiple of 16 bytes for
+    // every matrix: A 16-byte aligned and n even.
+    const bool bulk = ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && (n % 2 == 0);
+    const cudaError_t e = launch_eigh(nmax, g, A, W, V, info, batch, P, kp, counters, bulk, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return BED_OK;
+}
+
+}  // namespace
+
+}  // namespace bed
+
+extern "C" {
+
+void bed_default_params(bed_params* p)
+{
+    if (!p) return;
+    p->leaf_size = 2;
+    p->k_multisection = 4;
+    p->max_section_iters = 24;
+    p->max_halley_iters = 32;
+    p->section_rel_eps = 0x1p-6f;
+    p->stop_c = 8.f;
+    p->deflation_tol_scale = 8.f;
+    p->threads_per_matrix = 0;
+    p->retire_by_vote = 1;
+}
+
+bed_status bed_eigh_f32(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
+                        const bed_params* p, cudaStream_t stream)
+{
+    return bed::eigh_common(A, W, V, info, batch, n, p, nullptr, stream);
+}
+
+bed_status bed_eigh_f32_counted(const float* A, float* W, float* V, int32_t* info, int64_t batch,
+                                int n, const bed_params* p, bed_counters* counters,
+                                cudaStream_t stream)
+{
+    if (!counters) return BED_ERR_INVALID_ARG;
+    return bed::eigh_common(A, W, V, info, batch, n, p, counters, stream);
+}
+
+int bed_max_n(void) { return bed::kMaxN; }
+
+const char* bed_status_string(bed_status s)
+{
+    switch (s) {
+    case BED_OK: return "BED_OK";
+    case BED_ERR_INVALID_ARG: return "BED_ERR_INVALID_ARG";
+    case BED_ERR_UNSUPPORTED_N: return "BED_ERR_UNSUPPORTED_N";
+    case BED_ERR_CUDA: return "BED_ERR_CUDA";
+    }
+    return "BED_UNKNOWN_STATUS";
+}
+
+const char* bed_last_cuda_error(void) { return bed::g_last_cuda_error; }
+
+int bed_plan_describe(int n, int leaf_size, int* merges, int* level_of)
+{
+    bed::Plan P;
+    if (!bed::build_plan(n, leaf_size, &P)) return -1;
+    for (int L = 0; L < P.nlevels; ++L)
+        for (int i = P.level_start[L]; i < P.level_start[L + 1]; ++i) {
+            if (merges) {
+                merges[3 * i] = P.m_lo[i];
+                merges[3 * i + 1] = P.m_mid[i];
+                merges[3 * i + 2] = P.m_hi[i];
+            }
+            if (level_of) level_of[i] = L;
+        }
+    return P.nmerge;
+}
+
+}  // extern "C"

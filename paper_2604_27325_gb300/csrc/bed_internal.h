@@ -1,0 +1,54 @@
+// Internal declarations shared by the C-ABI layer and the kernel translation units.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime_api.h>
+
+#include "../../include/bed.h"
+
+namespace bed {
+
+constexpr int kMaxN = 64;
+constexpr int kMaxLevels = 8;  // merge levels of a tree over n <= 64 rows (6 with 1x1 leaves)
+
+// The divide tree of Sec. 2.1 for one n: blocks are split at floor(s/2) until they have at most
+// leaf_size rows. Passed by value to the kernel (a __grid_constant__ parameter), so every thread
+// reads it from the constant bank.
+struct Plan {
+    int n;
+    int nleaves;
+    int nmerge;
+    int nlevels;                            // merge levels; level 0 is the deepest
+    unsigned long long cut_mask;            // bit t: the tridiagonal is torn between rows t and t+1
+    uint8_t leaf_lo[kMaxN], leaf_hi[kMaxN]; // leaves [lo, hi), 1 or 2 rows
+    uint8_t m_lo[kMaxN], m_mid[kMaxN], m_hi[kMaxN];  // merges, grouped by level (deepest first)
+    uint8_t level_start[kMaxLevels + 1];    // merges of level L: [level_start[L], level_start[L+1])
+    uint8_t blk[kMaxLevels][kMaxN];         // merge that owns row/column t at level L, 0xFF if none
+};
+
+// Constants of the secular solver and deflation (bed_params minus the launch shape).
+struct KParams {
+    int k_ms;         // k of Eq. (16)
+    int max_sec;      // multi-section cap
+    int max_halley;   // Halley cap
+    float sec_eps;    // Eq. (17), relative to the initial bracket
+    float stop_c;     // Halley stop: |f| <= stop_c * u * err
+    float defl_c;     // deflation tolerance scale
+    int retire;       // warp-vote retirement of converged roots
+};
+
+bool build_plan(int n, int leaf_size, Plan* P);
+
+// One kernel launch over the whole batch. nmax in {16, 32, 64}, g in {2, 4} (threads = nmax * g).
+// bulk: stage each matrix with a TMA bulk copy (requires 16-byte aligned A and even n).
+cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int32_t* info,
+                        int64_t batch, const Plan& P, const KParams& kp, bed_counters* counters,
+                        bool bulk, cudaStream_t stream);
+
+template <int NMAX, int G>
+cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int64_t batch,
+                          const Plan& P, const KParams& kp, bed_counters* counters, bool bulk,
+                          cudaStream_t stream);
+
+}  // namespace bed

@@ -1,0 +1,114 @@
+"""The C ABI library loads, exports what include/bed.h declares, and validates arguments (CPU only).
+
+No call here reaches the GPU: every bed_eigh_f32 call below is rejected by argument validation (or
+has batch == 0) before anything is enqueued.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2604_27325_gb300 import binding as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bed.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bed_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = B.lib()
+    names = declared_functions()
+    assert names, "no declarations parsed"
+    for name in names:
+        assert hasattr(L, name), name
+    assert sorted(B.EXPORTED) == names
+
+
+def test_constants_and_strings():
+    assert B.bed_max_n() == 64
+    assert B.bed_status_string(B.BED_OK) == "BED_OK"
+    assert B.bed_status_string(B.BED_ERR_UNSUPPORTED_N) == "BED_ERR_UNSUPPORTED_N"
+    assert B.bed_status_string(99) == "BED_UNKNOWN_STATUS"
+    assert C.sizeof(B.bed_counters) == 32
+    p = B.bed_default_params()
+    assert (p.leaf_size, p.k_multisection, p.retire_by_vote, p.threads_per_matrix) == (2, 4, 1, 0)
+    assert p.section_rel_eps == 2.0**-6
+
+
+FAKE = 1 << 20  # aligned, never dereferenced: every call below is rejected before a launch
+
+
+@pytest.mark.parametrize("n", [0, -1, 65, 1000])
+def test_unsupported_n(n):
+    assert B.bed_eigh_f32(FAKE, FAKE, FAKE + 4096, None, 4, n) == B.BED_ERR_UNSUPPORTED_N
+
+
+def test_invalid_arguments_rejected_before_launch():
+    assert B.bed_eigh_f32(FAKE, FAKE, FAKE + 4096, None, -1, 8) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32(0, FAKE, FAKE, None, 3, 8) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32(FAKE, 0, FAKE, None, 3, 8) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32(FAKE, FAKE, 0, None, 3, 8) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32(FAKE + 2, FAKE, FAKE + 4096, None, 3, 8) == B.BED_ERR_INVALID_ARG  # misaligned
+    assert B.bed_eigh_f32(FAKE, FAKE, FAKE + 4096, FAKE + 1, 3, 8) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32(FAKE, FAKE, FAKE, None, 3, 8) == B.BED_ERR_INVALID_ARG  # V aliases A
+    assert B.bed_eigh_f32_counted(FAKE, FAKE, FAKE + 4096, None, 3, 8, None, 0) == B.BED_ERR_INVALID_ARG
+
+
+def test_empty_batch_is_ok_without_launch():
+    assert B.bed_eigh_f32(0, 0, 0, None, 0, 8) == B.BED_OK
+
+
+@pytest.mark.parametrize(
+    "field,value",
+    [("leaf_size", 3), ("leaf_size", 0), ("k_multisection", 1), ("max_halley_iters", 0),
+     ("max_section_iters", -1), ("section_rel_eps", 0.0), ("section_rel_eps", 1.0), ("stop_c", 0.5),
+     ("deflation_tol_scale", 0.0), ("retire_by_vote", 2), ("threads_per_matrix", 100)],
+)
+def test_bad_params(field, value):
+    p = B.make_params(**{field: value})
+    assert B.bed_eigh_f32(FAKE, FAKE, FAKE + 4096, None, 3, 8, p) == B.BED_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("leaf", [1, 2])
+def test_divide_tree_plan(leaf):
+    """Sec. 2.1 divide tree: split at floor(s/2) down to <= leaf rows; children merge before parents."""
+    for n in range(1, 65):
+        merges = B.bed_plan_describe(n, leaf)
+        # leaves = maximal blocks never split
+        splits = {(lo, hi): mid for lo, mid, hi, _ in merges}
+        lvl = {(lo, hi): L for lo, _, hi, L in merges}
+        nleaves = 0
+
+        def walk(lo, hi):
+            nonlocal nleaves
+            if hi - lo <= leaf:
+                assert (lo, hi) not in splits
+                nleaves += 1
+                return -1
+            mid = splits[(lo, hi)]
+            assert mid == lo + (hi - lo) // 2
+            l1, l2 = walk(lo, mid), walk(mid, hi)
+            assert lvl[(lo, hi)] > max(l1, l2)
+            return lvl[(lo, hi)]
+
+        walk(0, n)
+        assert len(merges) == nleaves - 1
+        assert [m[3] for m in merges] == sorted(m[3] for m in merges)  # deepest level first
+    with pytest.raises(ValueError):
+        B.bed_plan_describe(65)
+    with pytest.raises(ValueError):
+        B.bed_plan_describe(8, 3)
+
+
+def test_no_cpu_fallback():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(B.BedError):
+        B.batched_eigh(torch.eye(4).unsqueeze(0))

@@ -1,0 +1,185 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs (GPU)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_27325_gb300 import binding as B
+from paper_2604_27325_gb300 import workloads as wl
+from parity import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+NTHREADS = os.cpu_count() or 1
+
+
+def run_gpu(A, params=None, offset=0):
+    """A float32 numpy [b, n, n] -> (W, V, info) numpy, through bed_eigh_f32 on the current stream.
+    offset > 0 places A at a non-16-byte-aligned address (exercises the plain-load staging path)."""
+    b, n, _ = A.shape
+    flat = torch.zeros(A.size + 8, dtype=torch.float32, device="cuda")
+    Ad = flat[offset: offset + A.size].view(b, n, n)
+    Ad.copy_(torch.from_numpy(np.ascontiguousarray(A)))
+    W = torch.full((b, n), -7.0, device="cuda")
+    V = torch.full((b, n, n), -7.0, device="cuda")
+    info = torch.full((b,), -1, dtype=torch.int32, device="cuda")
+    st = B.bed_eigh_f32(Ad.data_ptr(), W.data_ptr(), V.data_ptr(), info.data_ptr(), b, n, params,
+                        torch.cuda.current_stream().cuda_stream)
+    assert st == B.BED_OK, B.bed_status_string(st)
+    torch.cuda.synchronize()
+    return W.cpu().numpy(), V.cpu().numpy(), info.cpu().numpy()
+
+
+def run_oracle(A):
+    Wo, Vo, st, _ = oracle.eigh_batch_f32(A, nthreads=NTHREADS)
+    assert st.not_conv == 0
+    return Wo, Vo
+
+
+# ----------------------------------------------------------------------------- the workloads
+
+
+def test_plain_known_spectrum_batch64_n16():
+    A, lam = wl.known_spectrum(64, 16, seed=wl.SEED_PLAIN)
+    W, V, info = run_gpu(A)
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W, V, info, Wo, Vo, "known spectrum 64 x 16")
+
+
+@pytest.mark.parametrize("n", [16, 32, 48, 64])
+def test_uniform_covariance_batch512(n):
+    A = wl.covariance(512, n)
+    W, V, info = run_gpu(A)
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W, V, info, Wo, Vo, f"covariance 512 x {n}")
+
+
+@pytest.mark.parametrize("n", list(range(1, 65)))
+def test_every_n_ragged_batch(n):
+    """Every supported size, both input families, a batch that is not a multiple of anything."""
+    A = np.concatenate([wl.covariance(5, n, seed=9000 + n), wl.known_spectrum(6, n, seed=9100 + n)[0]])
+    W, V, info = run_gpu(A)
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W, V, info, Wo, Vo, f"n={n}")
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 16, 17, 33, 64])
+@pytest.mark.parametrize("name", ["zero", "identity", "diagonal", "repeated", "rank_one", "block_diagonal", "toeplitz"])
+def test_degenerate_inputs(n, name):
+    A = wl.special_cases(n)[name][None].repeat(3, axis=0)
+    W, V, info = run_gpu(A)
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W, V, info, Wo, Vo, f"{name} n={n}")
+    if name == "diagonal":
+        assert np.array_equal(W[0], np.sort(np.diag(A[0])))
+
+
+def test_empty_batch():
+    W = torch.empty(0, 8, device="cuda")
+    assert B.bed_eigh_f32(0, W.data_ptr(), W.data_ptr() + 4, None, 0, 8) == B.BED_OK
+
+
+@pytest.mark.parametrize("n", [7, 16, 64])
+def test_upper_triangle_is_ignored(n):
+    A = wl.covariance(4, n, seed=77)
+    G = A.copy()
+    iu = np.triu_indices(n, 1)
+    G[:, iu[0], iu[1]] = np.float32(123.0)
+    W1, V1, _ = run_gpu(A)
+    W2, V2, _ = run_gpu(G)
+    assert np.array_equal(W1, W2) and np.array_equal(V1, V2)
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e-12, 1e12, 1e30])
+def test_extreme_scales(scale):
+    A = (wl.covariance(8, 32, seed=5).astype(np.float64) * scale).astype(np.float32)
+    W, V, info = run_gpu(A)
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W, V, info, Wo, Vo, f"scale {scale}")
+
+
+def test_nonfinite_input_flags_only_that_matrix():
+    A = wl.covariance(6, 12, seed=3)
+    A[2, 5, 1] = np.nan
+    A[4, 0, 0] = np.inf
+    W, V, info = run_gpu(A)
+    assert info[2] == B.BED_INFO_NONFINITE and info[4] == B.BED_INFO_NONFINITE
+    assert np.all(np.isnan(W[[2, 4]])) and np.all(np.isnan(V[[2, 4]]))
+    ok = [0, 1, 3, 5]
+    Wo, Vo = run_oracle(A[ok])
+    assert_parity(A[ok], W[ok], V[ok], info[ok], Wo, Vo, "finite matrices of a mixed batch")
+
+
+@pytest.mark.parametrize("n", [15, 16, 48])
+def test_unaligned_input_takes_the_plain_load_path_with_identical_results(n):
+    A = wl.covariance(9, n, seed=11)
+    W1, V1, i1 = run_gpu(A, offset=0)
+    W2, V2, i2 = run_gpu(A, offset=1)
+    assert np.array_equal(W1, W2) and np.array_equal(V1, V2) and np.array_equal(i1, i2)
+
+
+# ----------------------------------------------------------------------------- parameters
+
+
+@pytest.mark.parametrize("n", [16, 48, 64])
+def test_vote_retirement_is_result_neutral(n):
+    """Progressive shrinkage (Eq. (22)) recast as warp-vote retirement changes work, not results."""
+    A = wl.covariance(64, n, seed=21)
+    W1, V1, _ = run_gpu(A, B.make_params(retire_by_vote=1))
+    W0, V0, _ = run_gpu(A, B.make_params(retire_by_vote=0))
+    assert np.array_equal(W1, W0) and np.array_equal(V1, V0)
+
+
+@pytest.mark.parametrize(
+    "kw",
+    [dict(leaf_size=1), dict(k_multisection=2), dict(k_multisection=8, section_rel_eps=2.0**-10),
+     dict(section_rel_eps=0.5, max_section_iters=0), dict(threads_per_matrix=128)],
+)
+def test_parameter_variants_hold_tolerance(kw):
+    A = wl.covariance(32, 64 if kw.get("threads_per_matrix") == 128 else 40, seed=31)
+    W, V, info = run_gpu(A, B.make_params(**kw))
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W, V, info, Wo, Vo, str(kw))
+
+
+def test_counters():
+    A = wl.covariance(16, 32, seed=41)
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    Ad = torch.from_numpy(A).cuda()
+    W = torch.empty(16, 32, device="cuda")
+    V = torch.empty(16, 32, 32, device="cuda")
+    st = B.bed_eigh_f32_counted(Ad.data_ptr(), W.data_ptr(), V.data_ptr(), None, 16, 32, None, cnt.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+    assert st == B.BED_OK
+    torch.cuda.synchronize()
+    matrices, roots, evals, deflated = cnt.tolist()
+    assert matrices == 16
+    # each merge of size s yields s eigenpairs: roots + deflated = sum of merge sizes
+    total = 16 * sum(hi - lo for lo, _, hi, _ in B.bed_plan_describe(32))
+    assert roots + deflated == total
+    assert roots > 0 and evals > roots
+
+
+def test_host_buffers_end_to_end():
+    A = wl.covariance(8, 24, seed=51)
+    W, V, info = B.batched_eigh(torch.from_numpy(A), return_info=True)
+    assert not W.is_cuda
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W.numpy(), V.numpy(), info.numpy(), Wo, Vo, "host path")
+
+
+def test_large_batch_sampled():
+    """A batch much larger than the GPU's resident blocks; sampled matrices against the oracle."""
+    b, n = 4096, 64
+    A = wl.covariance(b, n, seed=61)
+    W, V, info = run_gpu(A)
+    assert np.all(info == 0)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(b, 48, replace=False))
+    Wo, Vo = run_oracle(A[idx])
+    assert_parity(A[idx], W[idx], V[idx], info[idx], Wo, Vo, "sampled large batch")
