@@ -3,19 +3,22 @@
 // One thread block solves one matrix at a time, entirely in shared memory:
 //   a0  stage A[b] into shared memory (TMA bulk copy + mbarrier, or coalesced loads), read the lower
 //       triangle, check finiteness, scale by a power of two
-//   a1  Householder tridiagonalization; the reflector dot products are warp-shuffle reductions
+//   a1  Householder tridiagonalization: reflector norms and p.v by warp shuffles, the matvec split
+//       over G lanes per row, two block barriers per reflector
 //   a2  tear the tridiagonal along the static divide tree (Sec. 2.1, Eq. (2)-(3))
 //   a3  2x2 leaves by one Jacobi rotation (Sec. 2.2)
 //   a4  per merge (Eq. (4)-(5)): coupling vector z, pole ordering, deflation
-//   a5  secular roots (Eq. (8)-(21)): one thread per root, hybrid-section then Halley in coordinates
+//   a5  secular roots (Eq. (8)-(21)): G lanes per root, hybrid-section then Halley in coordinates
 //       relative to the nearer pole; a warp stops iterating when all of its lanes have converged
 //       (the GPU form of the progressive batch shrinkage, Eq. (22))
 //   a6  Gu-Eisenstat z-hat (Eq. (25)) and normalized eigenvectors (Eq. (24))
 //   a7  merge GEMM Q <- blkdiag(Q1, Q2) Q^ (Eq. (4))
-//   a8  back-transform through the Householder reflectors
+//   a8  back-transform through the Householder reflectors, 8 at a time as I - Y T Y^T
 //   a9  ascending order, sign convention, store
-// Thread layout: NT = NMAX * G threads; "column" col = tid % NMAX, "group" grp = tid / NMAX. Phases
-// indexed by a row/column/root use threads tid < n.
+// Thread layouts (NT = NMAX * G threads):
+//   "position" pos = tid / G, sub = tid % G: G consecutive lanes share one row / column / root and
+//       combine their partial results with shuffles inside the group;
+//   "column"   col = tid % NMAX, grp = tid / NMAX: used by the rank updates and GEMM-like phases.
 #pragma once
 
 #include <cfloat>
@@ -28,32 +31,33 @@
 namespace bed {
 
 constexpr float kU = 0x1p-24f;  // unit roundoff of binary32
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBT = 8;          // reflectors per back-transform block
 
 template <int NMAX, int G>
 struct Smem {
     static constexpr int LD = NMAX + 1;  // odd stride: column walks hit distinct banks
+    static constexpr int NB = NMAX / 2;  // merges per level, at most
     float A[NMAX * LD];  // matrix; after a1 row k holds reflector k in columns k+2..n-1
     float Q[NMAX * LD];  // eigenvectors of the current blocks (block diagonal)
-    float M[NMAX * LD];  // staging of A[b] (dense n x n); merge workspace (rows = sorted poles)
-    float P[G * NMAX];   // per-group partial sums
-    float vv[NMAX], ww[NMAX];              // reflector v and w of the current step
+    float M[NMAX * LD];  // staging of A[b]; merge workspace (rows = sorted poles); a8 workspace
+    float pp[NMAX], vv[NMAX];              // a1: p = tau A22 v and v of the current reflector
     float d[NMAX], e[NMAX], tau[NMAX];     // tridiagonal and reflector scalars
     float lam[NMAX];                       // eigenvalue of each column of Q
     float ds[NMAX], zs[NMAX];              // merge: poles and z in ascending pole order
-    float cd[NMAX], cz[NMAX];              // merge: compacted (non-deflated first) poles and z
+    float cd[NMAX], cz[NMAX], cz2[NMAX];   // merge: compacted (non-deflated first) scaled poles, z, z^2
     float tq[NMAX], zh[NMAX];              // merge: root offsets from their poles, z-hat
     float rc[NMAX], rs[NMAX];              // merge: Givens deflation rotations (by sorted position)
     float sgn[NMAX];
-    float brho[NMAX], bnz[NMAX], btol[NMAX];  // per merge block: rho = |beta|, |z|, tolerance
-    float bsc[NMAX];  // per merge block: power of two that brings max(max|d|, rho|z|^2) into [0.5, 1)
+    float brho[NB], bnz[NB], btol[NB], bsc[NB];  // per merge of a level: |beta|, |z|, tolerance, scale
     int rank[NMAX];   // column c of the children -> its sorted position
     int inv[NMAX];    // compacted index -> sorted position
     int org[NMAX];    // root -> compacted index of the pole it is measured from
     int rotj[NMAX];   // sorted position -> rotation partner (-1: none)
     int defl[NMAX];
-    int bK[NMAX];     // per merge block: number of secular roots
-    int brot[NMAX];   // per merge block: close-pole rotations present
     int outc[NMAX];   // output column j <- column outc[j] of Q
+    int bK[NB];       // per merge of a level: number of secular roots
+    int brot[NB];     // per merge of a level: close-pole rotations present
     float red[32];
     int flag_rot;
     int info;
@@ -64,15 +68,55 @@ struct Smem {
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 
 __device__ __forceinline__ float warp_max(float v)
 {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
     return v;
+}
+
+// Reductions over the G lanes of a position group; every lane of the warp must call them. xor
+// partners combine the same two values in both lanes, so all G lanes obtain bitwise identical results.
+template <int G>
+__device__ __forceinline__ float gsum(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ int gsumi(int v)
+{
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ float gmax(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+template <int G>
+__device__ __forceinline__ float gprod(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) v *= __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// One-instruction reciprocal (relative error below 1 ulp); its argument here is a distance to a pole of
+// a secular problem scaled to unit size, far from the subnormal range.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // Sort key with a total order: NaN sorts last, ties broken by index by the callers.
@@ -109,10 +153,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 }
 
 // ---------------------------------------------------------------------------------------------
-// a5: one secular root (Eq. (8)) of the compacted, ascending poles d[0] < ... < d[K-1].
-// Root q lies in (d_q, d_{q+1}) for q < K-1 (Eq. (9)) and in (d_{K-1}, upper] for q = K-1
-// (Eq. (10)-(11)). Every participating lane of the warp (mask) runs the same number of loop trips,
-// so that the vote that retires the warp is taken convergently.
+// a5: one secular root (Eq. (8)) of the compacted, ascending, unit-scaled poles
+// d[0] < ... < d[K-1] with couplings z2[j] = z_j^2. Root q lies in (d_q, d_{q+1}) for q < K-1
+// (Eq. (9)) and in (d_{K-1}, upper] for q = K-1 (Eq. (10)-(11)). Called by EVERY lane of the warp (non-participating lanes pass
+// part = false): the G lanes of a root split the pole sums and combine them with shuffles, and the
+// vote that retires the warp is taken by all 32 lanes.
 // ---------------------------------------------------------------------------------------------
 struct RootOut {
     int org;      // pole index the offset is measured from (0..K-1)
@@ -121,38 +166,46 @@ struct RootOut {
     bool conv;
 };
 
-__device__ __forceinline__ RootOut secular_root(const float* __restrict__ d, const float* __restrict__ z,
-                                                int K, int q, float rho, const KParams& kp,
-                                                unsigned mask)
+template <int G>
+__device__ __forceinline__ RootOut secular_root(const float* __restrict__ d, const float* __restrict__ z2,
+                                                int K, int q, float rho, const KParams& kp, bool part,
+                                                int sub)
 {
     RootOut r{q, 0.f, 0, false};
-    bool done = false;
-    const bool top = (q == K - 1);
-    float L = 0.f, U;
-    if (!top) {
-        U = d[q + 1] - d[q];
-    } else {
+    bool done = !part;
+    const bool top = part && (q == K - 1);
+    float L = 0.f, U = 1.f;
+    {
         // Eq. (10)-(11): lambda_top <= d_top + rho |z|^2 and lambda_top <= |D + rho z z^T|_F.
-        // Both bounds are raised by their FP32 rounding error so the bracket keeps the root.
+        // Both bounds are raised by their FP32 rounding error so that the bracket keeps the root.
         float zn2 = 0.f, sd2 = 0.f, sdz = 0.f, sdza = 0.f;
-        for (int j = 0; j < K; ++j) {
-            const float z2 = z[j] * z[j];
-            zn2 += z2;
-            sd2 = fmaf(d[j], d[j], sd2);
-            sdz = fmaf(d[j], z2, sdz);
-            sdza = fmaf(fabsf(d[j]), z2, sdza);
-        }
-        U = rho * zn2 * (1.f + 2.f * (K + 2) * kU);
-        const float rz = rho * zn2;
-        const float fro2 = fmaf(rz, rz, fmaf(2.f * rho, sdz, sd2));
-        const float err2 = 4.f * (K + 4) * kU * fmaf(rz, rz, fmaf(2.f * rho, sdza, sd2));
-        const float fro = sqrtf(fmaxf(fro2 + err2, 0.f));
-        const float uf = (fro - d[K - 1]) + 4.f * kU * (fro + fabsf(d[K - 1]));
-        if (uf > 0.f && uf < U) U = uf;
-        if (K == 1) {  // one pole: 1 + rho z^2/(d - lambda) = 0 has lambda = d + rho z^2
-            r.tau = rho * z[0] * z[0];
-            r.conv = true;
-            done = true;
+        if (top)
+            for (int j = sub; j < K; j += G) {
+                const float zz = z2[j];
+                zn2 += zz;
+                sd2 = fmaf(d[j], d[j], sd2);
+                sdz = fmaf(d[j], zz, sdz);
+                sdza = fmaf(fabsf(d[j]), zz, sdza);
+            }
+        zn2 = gsum<G>(zn2);
+        sd2 = gsum<G>(sd2);
+        sdz = gsum<G>(sdz);
+        sdza = gsum<G>(sdza);
+        if (top) {
+            U = rho * zn2 * (1.f + 2.f * (K + 2) * kU);
+            const float rz = rho * zn2;
+            const float fro2 = fmaf(rz, rz, fmaf(2.f * rho, sdz, sd2));
+            const float err2 = 4.f * (K + 4) * kU * fmaf(rz, rz, fmaf(2.f * rho, sdza, sd2));
+            const float fro = sqrtf(fmaxf(fro2 + err2, 0.f));
+            const float uf = (fro - d[K - 1]) + 4.f * kU * (fro + fabsf(d[K - 1]));
+            if (uf > 0.f && uf < U) U = uf;
+            if (K == 1) {  // one pole: 1 + rho z^2/(d - lambda) = 0 has lambda = d + rho z^2
+                r.tau = rho * z2[0];
+                r.conv = true;
+                done = true;
+            }
+        } else if (part) {
+            U = d[q + 1] - d[q];
         }
     }
     const float width0 = U;
@@ -163,22 +216,34 @@ __device__ __forceinline__ RootOut secular_root(const float* __restrict__ d, con
     const float kinv = 1.f / static_cast<float>(kp.k_ms);
     const int cap = 2 + kp.max_sec + kp.max_halley;
     for (int it = 0; it < cap; ++it) {
-        if (kp.retire && !__any_sync(mask, !done)) break;  // progressive shrinkage (Eq. (22))
-        if (done) continue;
-        // Eq. (8), (18), (21) at lambda = d[o] + h, with d_j - lambda = (d_j - d_o) - h
+        if (kp.retire && !__any_sync(kFull, !done)) break;  // progressive shrinkage (Eq. (22))
+        // Eq. (8) at lambda = d[o] + h, with d_j - lambda = (d_j - d_o) - h; the sectioning steps need
+        // only the sign of f, Halley's steps also f' (Eq. (18)), f'' (Eq. (21)) and the error scale
+        const bool deriv = __any_sync(kFull, !done && state == 2);
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, sa = 0.f;
-        const float dorg = d[o];
-        for (int j = 0; j < K; ++j) {
-            const float del = (d[j] - dorg) - h;
-            const float inv = __frcp_rn(del);
-            const float zj = z[j];
-            const float t = zj * zj * inv;
-            const float ti = t * inv;
-            s0 += t;
-            s1 += ti;
-            s2 = fmaf(ti, inv, s2);
-            sa += fabsf(t);
+        if (!done) {
+            const float dorg = d[o];
+            if (deriv) {
+                for (int j = sub; j < K; j += G) {
+                    const float inv = rcp_approx((d[j] - dorg) - h);
+                    const float t = z2[j] * inv;
+                    const float ti = t * inv;
+                    s0 += t;
+                    s1 += ti;
+                    s2 = fmaf(ti, inv, s2);
+                    sa += fabsf(t);
+                }
+            } else {
+                for (int j = sub; j < K; j += G) s0 = fmaf(z2[j], rcp_approx((d[j] - dorg) - h), s0);
+            }
         }
+        s0 = gsum<G>(s0);
+        if (deriv) {
+            s1 = gsum<G>(s1);
+            s2 = gsum<G>(s2);
+            sa = gsum<G>(sa);
+        }
+        if (done) continue;
         const float f = fmaf(rho, s0, 1.f);
         const float f1 = rho * s1;
         const float f2 = 2.f * rho * s2;
@@ -245,7 +310,7 @@ __device__ __forceinline__ RootOut secular_root(const float* __restrict__ d, con
 // The kernel
 // ---------------------------------------------------------------------------------------------
 template <int NMAX, int G>
-__global__ void __launch_bounds__(NMAX * G)
+__global__ void __launch_bounds__(NMAX * G, 65536 / (NMAX * G * 64))
     eigh_kernel(const float* __restrict__ A, float* __restrict__ W, float* __restrict__ V,
                 int32_t* __restrict__ info, int64_t batch, const __grid_constant__ Plan plan,
                 const KParams kp, bed_counters* __restrict__ counters, int bulk)
@@ -253,7 +318,7 @@ __global__ void __launch_bounds__(NMAX * G)
     constexpr int NT = NMAX * G;
     constexpr int NW = NT / 32;
     constexpr int LD = Smem<NMAX, G>::LD;
-    constexpr int RPT = NMAX / G;  // merge-GEMM rows per thread
+    constexpr int RPT = NMAX / G;  // rows per thread in the column layout
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<NMAX, G>& S = *reinterpret_cast<Smem<NMAX, G>*>(smem_raw);
 
@@ -262,6 +327,8 @@ __global__ void __launch_bounds__(NMAX * G)
     const int warp = tid >> 5;
     const int col = tid % NMAX;
     const int grp = tid / NMAX;
+    const int pos = tid / G;
+    const int sub = tid % G;
     const int n = plan.n;
     const uint32_t bar = smem_u32(&S.mbar);
     uint32_t phase = 0;
@@ -370,39 +437,25 @@ __global__ void __launch_bounds__(NMAX * G)
                 tau = (beta - alpha) / beta;
                 scal = 1.f / (alpha - beta);
             }
-            // partial products p = A22 v over row groups
-            if (col < m) {
-                const int i = r0 + col;
+            // p = tau A22 v with v = [1, scal x]: p_i = tau (A[r0][i] + scal sum_{j>r0} A[j][i] x_j).
+            // G lanes per row i, each over interleaved runs of 8 columns j (the runs of the G lanes of
+            // 32/G consecutive rows fall in distinct banks)
+            {
                 float acc = 0.f;
-                for (int j = r0 + grp; j < n; j += G) {
-                    const float vj = (j == r0) ? 1.f : S.A[k * LD + j] * scal;
-                    acc = fmaf(S.A[j * LD + i], vj, acc);
+                const int i = r0 + pos;
+                if (pos < m) {
+#pragma unroll
+                    for (int blk = 0; blk < (NMAX + 8 * G - 1) / (8 * G); ++blk)
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int j = r0 + 1 + 8 * (sub + G * blk) + u;
+                            if (j < n) acc = fmaf(S.A[j * LD + i], S.A[k * LD + j], acc);
+                        }
                 }
-                S.P[grp * NMAX + i] = acc;
-                if (grp == 0) S.vv[i] = (i == r0) ? 1.f : S.A[k * LD + i] * scal;
-            }
-            __syncthreads();
-            // w = p - (tau/2)(p.v) v with p = tau A22 v
-            if (warp == 0) {
-                float pl[2] = {0.f, 0.f};
-                float pvp = 0.f;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = r0 + lane + 32 * h;
-                    if (i < n) {
-                        float p = 0.f;
-#pragma unroll
-                        for (int g = 0; g < G; ++g) p += S.P[g * NMAX + i];
-                        p *= tau;
-                        pl[h] = p;
-                        pvp = fmaf(p, S.vv[i], pvp);
-                    }
-                }
-                const float c = 0.5f * tau * warp_sum(pvp);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = r0 + lane + 32 * h;
-                    if (i < n) S.ww[i] = fmaf(-c, S.vv[i], pl[h]);
+                acc = gsum<G>(acc);
+                if (pos < m && sub == 0) {
+                    S.pp[i] = tau * fmaf(scal, acc, S.A[r0 * LD + i]);
+                    S.vv[i] = (i == r0) ? 1.f : S.A[k * LD + i] * scal;
                 }
             }
             if (tid == 0) {
@@ -411,13 +464,22 @@ __global__ void __launch_bounds__(NMAX * G)
                 S.tau[k] = tau;
             }
             __syncthreads();
-            // A22 -= v w^T + w v^T; row k keeps v (columns r0+1..n-1)
-            if (col < m) {
-                const int j = r0 + col;
-                const float vj = S.vv[j], wj = S.ww[j];
-                for (int i = r0 + grp; i < n; i += G)
-                    S.A[i * LD + j] -= fmaf(S.vv[i], wj, S.ww[i] * vj);
-                if (grp == 0 && j > r0) S.A[k * LD + j] = vj;
+            // w = p - (tau/2)(p.v) v (every warp forms p.v); A22 -= v w^T + w v^T; row k keeps v
+            {
+                float pvp = 0.f;
+                for (int i = r0 + lane; i < n; i += 32) pvp = fmaf(S.pp[i], S.vv[i], pvp);
+                const float c = 0.5f * tau * warp_sum(pvp);
+                if (col < m) {
+                    const int j = r0 + col;
+                    const float vj = S.vv[j];
+                    const float wj = fmaf(-c, vj, S.pp[j]);
+                    for (int i = r0 + grp; i < n; i += G) {
+                        const float vi = S.vv[i];
+                        const float wi = fmaf(-c, vi, S.pp[i]);
+                        S.A[i * LD + j] -= fmaf(vi, wj, wi * vj);
+                    }
+                    if (grp == 0 && j > r0) S.A[k * LD + j] = vj;
+                }
             }
             __syncthreads();
         }
@@ -468,8 +530,11 @@ __global__ void __launch_bounds__(NMAX * G)
 
         // ---------------- a4-a7: merges, deepest level first -----------------------------------
         for (int L = 0; L < plan.nlevels; ++L) {
-            const int bi = (tid < n) ? plan.blk[L][tid] : 0xFF;
+            const int l0 = plan.level_start[L];
+            // position layout: this group's row/column/root t = pos belongs to merge bi
+            const int bi = (pos < n) ? plan.blk[L][pos] : 0xFF;
             const bool act = (bi != 0xFF);
+            const int lb = bi - l0;  // merge index within the level
             int lo = 0, mid = 0, hi = 0;
             if (act) {
                 lo = plan.m_lo[bi];
@@ -477,45 +542,52 @@ __global__ void __launch_bounds__(NMAX * G)
                 hi = plan.m_hi[bi];
             }
             // P1: z (Eq. (5)), pole order, block scalars
-            if (act) {
-                const int c = tid;
-                const float beta = S.e[mid - 1];
-                const float rho = fabsf(beta);
-                const float sig = (beta >= 0.f) ? 1.f : -1.f;
-                const float* z1 = &S.Q[(mid - 1) * LD];  // last row of Q1
-                const float* z2 = &S.Q[mid * LD];        // first row of Q2
-                const float zc = (c < mid) ? sig * z1[c] : z2[c];
-                const float kc = sort_key(S.lam[c]);
+            {
+                const int c = pos;
+                float zc = 0.f, kc = 0.f;
                 int p = 0;
                 float nz2 = 0.f, dmax = 0.f;
-                for (int c2 = lo; c2 < hi; ++c2) {
-                    const float l2 = S.lam[c2];
-                    const float k2 = sort_key(l2);
-                    p += (k2 < kc) || (k2 == kc && c2 < c);
-                    const float zz = (c2 < mid) ? z1[c2] : z2[c2];
-                    nz2 = fmaf(zz, zz, nz2);
-                    dmax = fmaxf(dmax, fabsf(l2));
+                if (act) {
+                    const float sig = (S.e[mid - 1] >= 0.f) ? 1.f : -1.f;
+                    const float* z1 = &S.Q[(mid - 1) * LD];  // last row of Q1
+                    const float* z2 = &S.Q[mid * LD];        // first row of Q2
+                    zc = (c < mid) ? sig * z1[c] : z2[c];
+                    kc = sort_key(S.lam[c]);
+                    for (int c2 = lo + sub; c2 < hi; c2 += G) {
+                        const float l2 = S.lam[c2];
+                        const float k2 = sort_key(l2);
+                        p += (k2 < kc) || (k2 == kc && c2 < c);
+                        const float zz = (c2 < mid) ? z1[c2] : z2[c2];
+                        nz2 = fmaf(zz, zz, nz2);
+                        dmax = fmaxf(dmax, fabsf(l2));
+                    }
                 }
-                S.rank[c] = lo + p;
-                S.ds[lo + p] = S.lam[c];
-                S.zs[lo + p] = zc;
-                if (c == lo) {
-                    const float bscale = fmaxf(dmax, rho * nz2);
-                    int ex = 0;
-                    if (bscale > 0.f) frexpf(bscale, &ex);
-                    S.brho[bi] = rho;
-                    S.bnz[bi] = sqrtf(nz2);
-                    S.btol[bi] = kp.defl_c * kU * bscale;
-                    S.bsc[bi] = ldexpf(1.f, -ex);
-                    S.brot[bi] = 0;
+                p = gsumi<G>(p);
+                nz2 = gsum<G>(nz2);
+                dmax = gmax<G>(dmax);
+                if (act && sub == 0) {
+                    S.rank[c] = lo + p;
+                    S.ds[lo + p] = S.lam[c];
+                    S.zs[lo + p] = zc;
+                    if (c == lo) {
+                        const float rho = fabsf(S.e[mid - 1]);
+                        const float bscale = fmaxf(dmax, rho * nz2);
+                        int bex = 0;
+                        if (bscale > 0.f) frexpf(bscale, &bex);
+                        S.brho[lb] = rho;
+                        S.bnz[lb] = sqrtf(nz2);
+                        S.btol[lb] = kp.defl_c * kU * bscale;
+                        S.bsc[lb] = ldexpf(1.f, -bex);
+                        S.brot[lb] = 0;
+                    }
                 }
             }
             if (tid == 0) S.flag_rot = 0;
             __syncthreads();
             // P2: deflation of negligible couplings; detect close-pole pairs
-            if (act) {
-                const int t = tid;
-                const float rho = S.brho[bi], nz = S.bnz[bi], tol = S.btol[bi];
+            if (act && sub == 0) {
+                const int t = pos;
+                const float rho = S.brho[lb], nz = S.bnz[lb], tol = S.btol[lb];
                 const float zp = S.zs[t];
                 const int dfl = (rho * fabsf(zp) * nz <= tol);
                 S.defl[t] = dfl;
@@ -528,7 +600,7 @@ __global__ void __launch_bounds__(NMAX * G)
                         const float r = hypotf(zp, zj);
                         const float cc = zj / r, ss = zp / r;
                         if (fabsf((S.ds[j] - S.ds[t]) * cc * ss) <= tol) {
-                            S.brot[bi] = 1;
+                            S.brot[lb] = 1;
                             S.flag_rot = 1;
                         }
                     }
@@ -537,8 +609,8 @@ __global__ void __launch_bounds__(NMAX * G)
             __syncthreads();
             // P3: close-pole Givens deflation, one pass in pole order (rare)
             if (S.flag_rot) {
-                if (act && tid == lo && S.brot[bi]) {
-                    const float tol = S.btol[bi];
+                if (act && sub == 0 && pos == lo && S.brot[lb]) {
+                    const float tol = S.btol[lb];
                     int pj = -1;
                     for (int p = lo; p < hi; ++p) {
                         if (S.defl[p]) continue;
@@ -567,90 +639,111 @@ __global__ void __launch_bounds__(NMAX * G)
             // P4: compaction, non-deflated poles first (ascending). The secular problem of the block is
             // scaled exactly by a power of two to unit size: the derivatives of f grow like
             // 1/(d - lambda)^3 and would overflow FP32 for blocks whose spectrum is far below 1
-            if (act) {
-                const int t = tid;
-                const float sc = S.bsc[bi];
+            {
+                const int t = pos;
                 int nb = 0, K = 0;
-                for (int p = lo; p < hi; ++p) {
-                    const int nd = !S.defl[p];
-                    K += nd;
-                    nb += (p < t) & nd;
-                }
-                const int q = S.defl[t] ? (K + (t - lo - nb)) : nb;
-                S.inv[lo + q] = t;
-                S.cd[lo + q] = S.ds[t] * sc;
-                S.cz[lo + q] = S.zs[t];
-                if (t == lo) {
-                    S.bK[bi] = K;
-                    atomicAdd(&S.deflated, static_cast<unsigned>(hi - lo - K));
+                if (act)
+                    for (int p = lo + sub; p < hi; p += G) {
+                        const int nd = !S.defl[p];
+                        K += nd;
+                        nb += (p < t) & nd;
+                    }
+                nb = gsumi<G>(nb);
+                K = gsumi<G>(K);
+                if (act && sub == 0) {
+                    const int q = S.defl[t] ? (K + (t - lo - nb)) : nb;
+                    S.inv[lo + q] = t;
+                    S.cd[lo + q] = S.ds[t] * S.bsc[lb];
+                    S.cz[lo + q] = S.zs[t];
+                    S.cz2[lo + q] = S.zs[t] * S.zs[t];
+                    if (t == lo) {
+                        S.bK[lb] = K;
+                        atomicAdd(&S.deflated, static_cast<unsigned>(hi - lo - K));
+                    }
                 }
             }
             __syncthreads();
-            // P5: secular roots, one thread per root
+            // P5: secular roots, G lanes per root
             {
                 int K = 0, q = 0;
+                float sc = 1.f, rho = 0.f;
                 if (act) {
-                    K = S.bK[bi];
-                    q = tid - lo;
+                    K = S.bK[lb];
+                    q = pos - lo;
+                    sc = S.bsc[lb];
+                    rho = S.brho[lb] * sc;
                 }
                 const bool part = act && (q < K);
-                const unsigned mask = __ballot_sync(0xffffffffu, part);
-                if (part) {
-                    const float sc = S.bsc[bi];
-                    const RootOut r = secular_root(S.cd + lo, S.cz + lo, K, q, S.brho[bi] * sc, kp, mask);
-                    S.org[lo + q] = lo + r.org;
-                    S.tq[lo + q] = r.tau;
-                    S.lam[lo + q] = (S.cd[lo + r.org] + r.tau) * (1.f / sc);
-                    atomicAdd(&S.evals, static_cast<unsigned>(r.evals));
-                    atomicAdd(&S.roots, 1u);
-                    if (!r.conv) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
-                } else if (act) {
-                    S.org[lo + q] = lo + q;
-                    S.tq[lo + q] = 0.f;
-                    S.lam[lo + q] = S.cd[lo + q] * (1.f / S.bsc[bi]);
+                const RootOut r = secular_root<G>(S.cd + lo, S.cz2 + lo, K, q, rho, kp, part, sub);
+                if (sub == 0) {
+                    if (part) {
+                        S.org[lo + q] = lo + r.org;
+                        S.tq[lo + q] = r.tau;
+                        S.lam[lo + q] = (S.cd[lo + r.org] + r.tau) * (1.f / sc);
+                        atomicAdd(&S.evals, static_cast<unsigned>(r.evals));
+                        atomicAdd(&S.roots, 1u);
+                        if (!r.conv) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
+                    } else if (act) {
+                        S.org[lo + q] = lo + q;
+                        S.tq[lo + q] = 0.f;
+                        S.lam[lo + q] = S.cd[lo + q] * (1.f / sc);
+                    }
                 }
             }
             __syncthreads();
-            // P6: Gu-Eisenstat z-hat, Eq. (25), as a product of interlaced ratios
-            if (act) {
-                const int K = S.bK[bi];
-                const int i = tid - lo;
-                if (i < K) {
+            // P6: Gu-Eisenstat z-hat, Eq. (25), as a product of interlaced ratios, each in (0, 1):
+            //   (lambda_{K-1} - d_i)/rho * prod_{j<i} (lambda_j - d_i)/(d_j - d_i)
+            //                            * prod_{i<=j<K-1} (lambda_j - d_i)/(d_{j+1} - d_i)
+            {
+                int K = 0;
+                if (act) K = S.bK[lb];
+                const int i = pos - lo;
+                const bool own = act && (i < K);
+                float prod = 1.f;
+                if (own) {
                     const float di = S.cd[lo + i];
-                    const float rho = S.brho[bi] * S.bsc[bi];
-                    // (lambda_{K-1} - d_i)/rho first: it is the only factor that may exceed 1, so the
-                    // running product falls monotonically to its result and cannot underflow early
-                    float prod = ((S.cd[S.org[lo + K - 1]] - di) + S.tq[lo + K - 1]) / rho;
-                    for (int j = 0; j < K - 1; ++j) {
+                    if (sub == 0)
+                        prod = ((S.cd[S.org[lo + K - 1]] - di) + S.tq[lo + K - 1]) / (S.brho[lb] * S.bsc[lb]);
+                    for (int j = sub; j < K - 1; j += G) {
                         const float num = (S.cd[S.org[lo + j]] - di) + S.tq[lo + j];  // lambda_j - d_i
                         const float den = (j < i) ? (S.cd[lo + j] - di) : (S.cd[lo + j + 1] - di);
                         prod *= num / den;
                     }
-                    S.zh[lo + i] = copysignf(sqrtf(fmaxf(prod, 0.f)), S.cz[lo + i]);
                 }
+                prod = gprod<G>(prod);
+                if (own && sub == 0) S.zh[lo + i] = copysignf(sqrtf(fmaxf(prod, 0.f)), S.cz[lo + i]);
             }
             __syncthreads();
             // P7: eigenvectors of the merge (Eq. (24)) in sorted-pole rows, rotations undone
-            if (act) {
-                const int K = S.bK[bi];
-                const int q = tid - lo;
-                const int cq = tid;
-                for (int p = lo; p < hi; ++p) S.M[p * LD + cq] = 0.f;
-                if (q < K) {
-                    const float dorg = S.cd[S.org[lo + q]];
-                    const float tq = S.tq[lo + q];
-                    float nrm2 = 0.f;
-                    for (int i = 0; i < K; ++i) {
-                        const float v = S.zh[lo + i] / ((S.cd[lo + i] - dorg) - tq);
-                        S.M[S.inv[lo + i] * LD + cq] = v;
-                        nrm2 = fmaf(v, v, nrm2);
+            {
+                int K = 0;
+                if (act) K = S.bK[lb];
+                const int q = pos - lo;
+                const int cq = pos;
+                float nrm2 = 0.f;
+                if (act) {
+                    if (q < K) {
+                        const float dorg = S.cd[S.org[lo + q]];
+                        const float tq = S.tq[lo + q];
+                        for (int i = sub; i < K; i += G) {
+                            const float v = __fdividef(S.zh[lo + i], (S.cd[lo + i] - dorg) - tq);
+                            S.M[S.inv[lo + i] * LD + cq] = v;
+                            nrm2 = fmaf(v, v, nrm2);
+                        }
+                        for (int p = lo + sub; p < hi; p += G)
+                            if (S.defl[p]) S.M[p * LD + cq] = 0.f;
+                    } else {
+                        const int tgt = S.inv[lo + q];
+                        for (int p = lo + sub; p < hi; p += G) S.M[p * LD + cq] = (p == tgt) ? 1.f : 0.f;
                     }
-                    const float inv = 1.f / sqrtf(nrm2);
-                    for (int i = 0; i < K; ++i) S.M[S.inv[lo + i] * LD + cq] *= inv;
-                } else {
-                    S.M[S.inv[lo + q] * LD + cq] = 1.f;
                 }
-                if (S.brot[bi]) {
+                nrm2 = gsum<G>(nrm2);
+                if (act && q < K) {
+                    const float inv = rsqrtf(nrm2);
+                    for (int i = sub; i < K; i += G) S.M[S.inv[lo + i] * LD + cq] *= inv;
+                }
+                __syncwarp();
+                if (act && sub == 0 && S.brot[lb]) {
                     for (int p = hi - 1; p >= lo; --p) {
                         const int j = S.rotj[p];
                         if (j >= 0) {
@@ -696,57 +789,160 @@ __global__ void __launch_bounds__(NMAX * G)
             __syncthreads();
         }
 
-        // ---------------- a8: back-transform V = H_0 ... H_{n-3} Q_T --------------------------
-        for (int k = n - 3; k >= 0; --k) {
-            const float tk = S.tau[k];
-            if (tk == 0.f) continue;
-            const int r0 = k + 1;
-            if (col < n) {
-                float acc = 0.f;
-                for (int i = r0 + grp; i < n; i += G) {
-                    const float vi = (i == r0) ? 1.f : S.A[k * LD + i];
-                    acc = fmaf(vi, S.Q[i * LD + col], acc);
+        // ---------------- a8: back-transform V = H_0 ... H_{n-3} Q_T ----------------------------
+        // Blocks of kBT reflectors: H_{k0} ... H_{k0+b-1} = I - Y T Y^T with T upper triangular
+        // (forward accumulation); Y[i][r] = v_{k0+r}[i] is 0 above row k0+r+1, 1 on it and row k0+r
+        // of A below it. Blocks are applied last to first: Q <- Q - Y (T (Y^T Q)).
+        if (n >= 3) {
+            const int nr = n - 2;
+            const int ngr = (nr + kBT - 1) / kBT;
+            float* Tm = S.M;                    // ngr blocks of kBT x kBT: T above the diagonal, Gram below
+            float* W1 = S.M + ngr * kBT * kBT;  // kBT x NMAX
+            for (int g = warp; g < ngr; g += NW) {
+                const int k0 = g * kBT;
+                const int bsz = min(kBT, nr - k0);
+                float* T = Tm + g * kBT * kBT;
+                // Gram entries Y[:, r]^T Y[:, j] for r < j, one pair per lane, stored at T[j][r]
+                int p = lane, r = 0;
+                while (r < kBT - 1 && p >= kBT - 1 - r) {
+                    p -= kBT - 1 - r;
+                    ++r;
                 }
-                S.P[grp * NMAX + col] = acc;
+                const int j = r + 1 + p;
+                if (r < kBT - 1 && j < bsz) {
+                    const int kr = k0 + r, kj = k0 + j;
+                    float s = S.A[kr * LD + kj + 1];  // Y[kj+1][r] times Y[kj+1][j] = 1
+                    for (int i = kj + 2; i < n; ++i) s = fmaf(S.A[kr * LD + i], S.A[kj * LD + i], s);
+                    T[j * kBT + r] = s;
+                }
+                __syncwarp();
+                // T[jj][jj] = tau_jj; T[0:jj, jj] = T[0:jj, 0:jj] w with w_s = -tau_jj Gram[s][jj]
+                for (int jj = 0; jj < bsz; ++jj) {
+                    const float tj = S.tau[k0 + jj];
+                    const float w = (lane < jj) ? -tj * T[jj * kBT + lane] : 0.f;
+                    float acc = 0.f;
+                    for (int s2 = 0; s2 < jj; ++s2) {
+                        const float ws = __shfl_sync(kFull, w, s2);
+                        if (lane <= s2) acc = fmaf(T[lane * kBT + s2], ws, acc);
+                    }
+                    __syncwarp();
+                    if (lane < jj) T[lane * kBT + jj] = acc;
+                    if (lane == jj) T[jj * kBT + jj] = tj;
+                    __syncwarp();
+                }
             }
             __syncthreads();
-            if (col < n) {
-                float w = 0.f;
+            for (int g = ngr - 1; g >= 0; --g) {
+                const int k0 = g * kBT;
+                const int bsz = min(kBT, nr - k0);
+                const float* T = Tm + g * kBT * kBT;
+                // W1 = Y^T Q (bsz x n): this thread's rows r = grp + G*rr of W1, one pass over Q's column;
+                // rows i <= k0 + kBT hold the unit and zero entries of Y, the rows below are plain
+                constexpr int RB = (kBT + G - 1) / G;
+                if (col < n) {
+                    float acc[RB];
 #pragma unroll
-                for (int g = 0; g < G; ++g) w += S.P[g * NMAX + col];
-                w *= tk;
-                for (int i = r0 + grp; i < n; i += G) {
-                    const float vi = (i == r0) ? 1.f : S.A[k * LD + i];
-                    S.Q[i * LD + col] = fmaf(-vi, w, S.Q[i * LD + col]);
+                    for (int rr = 0; rr < RB; ++rr) acc[rr] = 0.f;
+                    const int iedge = min(k0 + kBT, n - 1);
+                    for (int i = k0 + 1; i <= iedge; ++i) {
+                        const float qv = S.Q[i * LD + col];
+#pragma unroll
+                        for (int rr = 0; rr < RB; ++rr) {
+                            const int kr = k0 + grp + G * rr;
+                            const float y = (i > kr + 1) ? S.A[kr * LD + i] : ((i == kr + 1) ? 1.f : 0.f);
+                            acc[rr] = fmaf(y, qv, acc[rr]);
+                        }
+                    }
+                    for (int i = iedge + 1; i < n; ++i) {
+                        const float qv = S.Q[i * LD + col];
+#pragma unroll
+                        for (int rr = 0; rr < RB; ++rr)
+                            acc[rr] = fmaf(S.A[(k0 + grp + G * rr) * LD + i], qv, acc[rr]);
+                    }
+#pragma unroll
+                    for (int rr = 0; rr < RB; ++rr) {
+                        const int r = grp + G * rr;
+                        if (r < bsz) W1[r * NMAX + col] = acc[rr];
+                    }
                 }
+                __syncthreads();
+                // Q -= Y (T W1)
+                if (col < n) {
+                    float w2[kBT];
+#pragma unroll
+                    for (int r = 0; r < kBT; ++r) {
+                        float s = 0.f;
+                        if (r < bsz)
+                            for (int s2 = r; s2 < bsz; ++s2) s = fmaf(T[r * kBT + s2], W1[s2 * NMAX + col], s);
+                        w2[r] = s;
+                    }
+                    // rows k0+r of A with r >= bsz are not reflectors (possibly never written): skip them
+                    int i = k0 + 1 + grp;
+                    for (; i <= k0 + kBT && i < n; i += G) {
+                        float acc = S.Q[i * LD + col];
+#pragma unroll
+                        for (int r = 0; r < kBT; ++r) {
+                            const int kr = k0 + r;
+                            if (r < bsz) {
+                                const float y = (i > kr + 1) ? S.A[kr * LD + i] : ((i == kr + 1) ? 1.f : 0.f);
+                                acc = fmaf(-y, w2[r], acc);
+                            }
+                        }
+                        S.Q[i * LD + col] = acc;
+                    }
+                    for (; i < n; i += G) {
+                        float acc = S.Q[i * LD + col];
+#pragma unroll
+                        for (int r = 0; r < kBT; ++r)
+                            if (r < bsz) acc = fmaf(-S.A[(k0 + r) * LD + i], w2[r], acc);
+                        S.Q[i * LD + col] = acc;
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
 
         // ---------------- a9: ascending order, signs, store ------------------------------------
-        if (tid < n) {
-            const float kc = sort_key(S.lam[tid]);
+        {
             int r = 0;
-            for (int t2 = 0; t2 < n; ++t2) {
-                const float k2 = sort_key(S.lam[t2]);
-                r += (k2 < kc) || (k2 == kc && t2 < tid);
-            }
-            S.outc[r] = tid;
-        }
-        __syncthreads();
-        if (tid < n) {
-            const int src = S.outc[tid];
-            int im = 0;
-            float vm = fabsf(S.Q[src]);
-            for (int i = 1; i < n; ++i) {
-                const float v = fabsf(S.Q[i * LD + src]);
-                if (v > vm) {
-                    vm = v;
-                    im = i;
+            if (pos < n) {
+                const float kc = sort_key(S.lam[pos]);
+                for (int t2 = sub; t2 < n; t2 += G) {
+                    const float k2 = sort_key(S.lam[t2]);
+                    r += (k2 < kc) || (k2 == kc && t2 < pos);
                 }
             }
-            S.sgn[tid] = (S.Q[im * LD + src] < 0.f) ? -1.f : 1.f;
-            Wb[tid] = S.lam[src] * unscale;
+            r = gsumi<G>(r);
+            if (pos < n && sub == 0) S.outc[r] = pos;
+        }
+        __syncthreads();
+        {
+            int src = 0;
+            float vm = -1.f;
+            int im = 0;
+            if (pos < n) {
+                src = S.outc[pos];
+                for (int i = sub; i < n; i += G) {
+                    const float v = fabsf(S.Q[i * LD + src]);
+                    if (v > vm) {
+                        vm = v;
+                        im = i;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = G / 2; o; o >>= 1) {
+                const float v2 = __shfl_xor_sync(kFull, vm, o);
+                const int i2 = __shfl_xor_sync(kFull, im, o);
+                if (v2 > vm || (v2 == vm && i2 < im)) {
+                    vm = v2;
+                    im = i2;
+                }
+            }
+            if (pos < n && sub == 0) {
+                S.sgn[pos] = (S.Q[im * LD + src] < 0.f) ? -1.f : 1.f;
+                Wb[pos] = S.lam[src] * unscale;
+            }
         }
         __syncthreads();
         for (int i = warp; i < n; i += NW)
@@ -773,6 +969,9 @@ cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int
     auto kern = eigh_kernel<NMAX, G>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
     if (err != cudaSuccess) return err;
     const int64_t max_grid = 2147483647LL;
     const unsigned grid = static_cast<unsigned>(batch < max_grid ? batch : max_grid);
