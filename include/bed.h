@@ -28,6 +28,7 @@
 #ifndef BED_H
 #define BED_H
 
+#include <stddef.h>
 #include <stdint.h>
 #include <cuda_runtime_api.h>
 
@@ -47,7 +48,8 @@ enum {
     BED_INFO_OK = 0,
     BED_INFO_NOT_CONVERGED = 1, /* a secular root hit the iteration cap; its last iterate is kept */
     BED_INFO_NONFINITE = 2,     /* A[b] held a NaN or an infinity: W[b] and V[b] are set to NaN */
-    BED_INFO_TIMEOUT = 4        /* the staging copy of A[b] did not complete in time: W[b], V[b] NaN */
+    BED_INFO_TIMEOUT = 4,       /* the staging copy of A[b] did not complete in time: W[b], V[b] NaN */
+    BED_INFO_BAD_N = 8          /* ragged batches: ns[b] outside [1, 64]; the matrix was skipped */
 };
 
 /*
@@ -104,6 +106,51 @@ typedef struct {
 bed_status bed_eigh_f32_counted(const float* A, float* W, float* V, int32_t* info, int64_t batch,
                                 int n, const bed_params* p, bed_counters* counters,
                                 cudaStream_t stream);
+
+/*
+ * Ragged batches: matrices of mixed size in one persistent launch (Sec. 2.1 notes that dividing turns a
+ * batch of B matrices into B*R blocks; here blocks of all sizes share the GPU in one launch).
+ *
+ * Work is handed out in units of one thread block (256 threads) split into teams, one matrix per team:
+ *   team type 0: 1 team of 256 threads, any n <= 64;   type 1: 2 teams of 128 threads, n <= 32;
+ *   type 2: 4 teams of 64 threads, n <= 16;            type 3: 8 teams of 32 threads, n <= 16.
+ * bed_ragged_tuning chooses the team type and the leaf size of the divide tree for every n (entries
+ * 1..64 are used; an autotuner fills it by measurement).
+ */
+typedef struct {
+    unsigned char team[65]; /* team type for each n */
+    unsigned char leaf[65]; /* leaf size (1 or 2) for each n */
+} bed_ragged_tuning;
+
+/* Fills *t with the built-in choice: type 2 for n <= 16, type 1 for n <= 32, type 0 above; leaf 2. */
+void bed_ragged_default_tuning(bed_ragged_tuning* t);
+
+/* Bytes of device workspace bed_eigh_ragged_f32 needs for `count` matrices (a multiple of 256). */
+size_t bed_eigh_ragged_workspace_size(int64_t count);
+
+/*
+ * Eigendecomposition of `count` symmetric FP32 matrices of mixed size, in one stream-ordered pair of
+ * launches (a one-block ordering pass, then the persistent kernel). All arrays are DEVICE memory:
+ *   A         packed matrices; matrix b is ns[b] x ns[b] row-major at A + offsets[b] (lower triangle read)
+ *   offsets   [count] int64 element offsets of each matrix in A, also used for V
+ *   ns        [count] int32 sizes; a size outside [1, 64] sets info[b] = BED_INFO_BAD_N and skips b
+ *   W         eigenvalues of matrix b (ascending) at W + w_offsets[b]
+ *   w_offsets [count] int64 element offsets into W
+ *   V         eigenvectors of matrix b (columns) at V + offsets[b]; V may not alias A
+ *   info      [count] int32 flags (may be NULL)
+ *   p         NULL or parameters (leaf_size and threads_per_matrix are ignored: the tuning decides)
+ *   tuning    NULL (built-in choice) or a host-side table, validated (a team type must fit its n)
+ *   workspace device memory of at least bed_eigh_ragged_workspace_size(count) bytes, 16-byte aligned,
+ *             owned by the caller; it must not be used by another call until this one completes
+ *   counters  NULL or a device bed_counters that the launch adds its work counts to
+ * The first call on a device performs a one-time setup of that device (it uploads the divide trees of
+ * every size, synchronously); make that first call before capturing calls into a CUDA graph. The calls
+ * themselves enqueue only kernel launches and can be captured and replayed.
+ */
+bed_status bed_eigh_ragged_f32(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count,
+                               float* W, const int64_t* w_offsets, float* V, int32_t* info,
+                               const bed_params* p, const bed_ragged_tuning* tuning, void* workspace,
+                               size_t workspace_bytes, bed_counters* counters, cudaStream_t stream);
 
 /* Largest supported n (64). */
 int bed_max_n(void);

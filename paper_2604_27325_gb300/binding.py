@@ -23,6 +23,7 @@ BED_INFO_OK = 0
 BED_INFO_NOT_CONVERGED = 1
 BED_INFO_NONFINITE = 2
 BED_INFO_TIMEOUT = 4
+BED_INFO_BAD_N = 8
 
 
 class bed_params(C.Structure):
@@ -48,10 +49,17 @@ class bed_counters(C.Structure):
     ]
 
 
+class bed_ragged_tuning(C.Structure):
+    _fields_ = [("team", C.c_ubyte * 65), ("leaf", C.c_ubyte * 65)]
+
+
 EXPORTED = [
     "bed_default_params",
     "bed_eigh_f32",
     "bed_eigh_f32_counted",
+    "bed_eigh_ragged_f32",
+    "bed_eigh_ragged_workspace_size",
+    "bed_ragged_default_tuning",
     "bed_max_n",
     "bed_status_string",
     "bed_last_cuda_error",
@@ -83,6 +91,13 @@ def lib() -> C.CDLL:
             L.bed_last_cuda_error.restype = C.c_char_p
             L.bed_plan_describe.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.bed_plan_describe.restype = C.c_int
+            L.bed_ragged_default_tuning.argtypes = [C.POINTER(bed_ragged_tuning)]
+            L.bed_ragged_default_tuning.restype = None
+            L.bed_eigh_ragged_workspace_size.argtypes = [C.c_int64]
+            L.bed_eigh_ragged_workspace_size.restype = C.c_size_t
+            L.bed_eigh_ragged_f32.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp, C.POINTER(bed_params),
+                                              C.POINTER(bed_ragged_tuning), vp, C.c_size_t, vp, vp]
+            L.bed_eigh_ragged_f32.restype = C.c_int
             _lib = L
         return _lib
 
@@ -107,6 +122,27 @@ def bed_eigh_f32_counted(A_ptr: int, W_ptr: int, V_ptr: int, info_ptr: int | Non
                          params: bed_params | None, counters_ptr: int, stream: int = 0) -> int:
     return lib().bed_eigh_f32_counted(A_ptr, W_ptr, V_ptr, info_ptr, batch, n,
                                       C.byref(params) if params is not None else None, counters_ptr, stream)
+
+
+def bed_ragged_default_tuning() -> bed_ragged_tuning:
+    t = bed_ragged_tuning()
+    lib().bed_ragged_default_tuning(C.byref(t))
+    return t
+
+
+def bed_eigh_ragged_workspace_size(count: int) -> int:
+    return int(lib().bed_eigh_ragged_workspace_size(count))
+
+
+def bed_eigh_ragged_f32(A_ptr: int, offsets_ptr: int, ns_ptr: int, count: int, W_ptr: int, w_offsets_ptr: int,
+                        V_ptr: int, info_ptr: int | None, params: bed_params | None, tuning: bed_ragged_tuning | None,
+                        workspace_ptr: int, workspace_bytes: int, counters_ptr: int | None = None,
+                        stream: int = 0) -> int:
+    """Raw call: device pointers as integers; returns the bed_status code."""
+    return lib().bed_eigh_ragged_f32(A_ptr, offsets_ptr, ns_ptr, count, W_ptr, w_offsets_ptr, V_ptr, info_ptr,
+                                     C.byref(params) if params is not None else None,
+                                     C.byref(tuning) if tuning is not None else None,
+                                     workspace_ptr, workspace_bytes, counters_ptr, stream)
 
 
 def bed_max_n() -> int:
@@ -206,3 +242,92 @@ def batched_eigh(A: torch.Tensor, params: bed_params | None = None, check: bool 
     V = V.reshape(*lead, n, n)
     info = info.reshape(lead)
     return (W, V, info) if return_info else (W, V)
+
+
+class RaggedBatch:
+    """Device-resident packed batch of matrices of mixed size (the ragged entry point's layout).
+
+    Matrices are packed back to back (each starting on a 16-byte boundary, so that even sizes can be
+    staged by bulk copy); outputs and the workspace are allocated once with PyTorch and reused by every
+    :meth:`solve`, which makes the call capturable into a CUDA graph (:meth:`capture`, :meth:`replay`).
+    """
+
+    def __init__(self, ns, device="cuda", params: bed_params | None = None, tuning: bed_ragged_tuning | None = None):
+        self.ns = [int(n) for n in ns]
+        self.count = len(self.ns)
+        off, woff = [], []
+        a = w = 0
+        for n in self.ns:
+            off.append(a)
+            woff.append(w)
+            a += (n * n + 3) // 4 * 4
+            w += n
+        self.offsets_list, self.woffsets_list = off, woff
+        self.device = torch.device(device)
+        self.A = torch.zeros(max(a, 4), dtype=torch.float32, device=self.device)
+        self.V = torch.zeros(max(a, 4), dtype=torch.float32, device=self.device)
+        self.W = torch.zeros(max(w, 1), dtype=torch.float32, device=self.device)
+        self.info = torch.zeros(max(self.count, 1), dtype=torch.int32, device=self.device)
+        self.offsets = torch.tensor(off or [0], dtype=torch.int64, device=self.device)
+        self.w_offsets = torch.tensor(woff or [0], dtype=torch.int64, device=self.device)
+        self.ns_dev = torch.tensor(self.ns or [1], dtype=torch.int32, device=self.device)
+        self.ws_bytes = bed_eigh_ragged_workspace_size(self.count)
+        self.workspace = torch.zeros(max(self.ws_bytes // 4, 4), dtype=torch.int32, device=self.device)
+        self.params = params
+        self.tuning = tuning
+        self.graph = None
+
+    def load(self, mats):
+        """Copy a list of n x n matrices (numpy or torch, any device) into the packed input."""
+        for k, M in enumerate(mats):
+            n = self.ns[k]
+            t = torch.as_tensor(M, dtype=torch.float32).reshape(-1)
+            self.A[self.offsets_list[k]: self.offsets_list[k] + n * n].copy_(t, non_blocking=True)
+        return self
+
+    def solve(self, counters: torch.Tensor | None = None, stream=None):
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        st = bed_eigh_ragged_f32(self.A.data_ptr(), self.offsets.data_ptr(), self.ns_dev.data_ptr(), self.count,
+                                 self.W.data_ptr(), self.w_offsets.data_ptr(), self.V.data_ptr(),
+                                 self.info.data_ptr(), self.params, self.tuning, self.workspace.data_ptr(),
+                                 self.ws_bytes, counters.data_ptr() if counters is not None else None, s)
+        _check(st)
+        return self
+
+    def capture(self):
+        """Record one solve into a CUDA graph (the first, setup-performing call is made beforehand)."""
+        self.solve()
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            g.capture_begin()
+            self.solve(stream=s)
+            g.capture_end()
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        self.graph = g
+        return self
+
+    def replay(self):
+        self.graph.replay()
+        return self
+
+    def results(self):
+        """List of (W, V) views, V with eigenvectors in columns."""
+        out = []
+        for k, n in enumerate(self.ns):
+            o, w = self.offsets_list[k], self.woffsets_list[k]
+            out.append((self.W[w: w + n], self.V[o: o + n * n].view(n, n)))
+        return out
+
+
+def batched_eigh_ragged(mats, params: bed_params | None = None, tuning: bed_ragged_tuning | None = None,
+                        return_info: bool = False):
+    """Eigendecompositions of a list of square FP32 matrices of mixed size (one persistent launch)."""
+    if not torch.cuda.is_available():
+        raise BedError("batched_eigh_ragged needs a CUDA device; there is no CPU path")
+    ns = [int(torch.as_tensor(M).shape[-1]) for M in mats]
+    rb = RaggedBatch(ns, params=params, tuning=tuning).load(mats).solve()
+    res = rb.results()
+    return (res, rb.info[: rb.count]) if return_info else res

@@ -97,22 +97,37 @@ cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int
 
 namespace {
 
+// Validates the parameters shared by every entry point and derives the kernel constants.
+bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
+{
+    bed_default_params(prm);
+    if (p) *prm = *p;
+    if (prm->leaf_size != 1 && prm->leaf_size != 2) return false;
+    if (prm->k_multisection < 2 || prm->k_multisection > 64) return false;
+    if (prm->max_section_iters < 0 || prm->max_section_iters > 256) return false;
+    if (prm->max_halley_iters < 1 || prm->max_halley_iters > 256) return false;
+    if (!(prm->section_rel_eps > 0.f && prm->section_rel_eps < 1.f)) return false;
+    if (!(prm->stop_c >= 1.f && prm->stop_c <= 1e6f)) return false;
+    if (!(prm->deflation_tol_scale >= 1.f && prm->deflation_tol_scale <= 1e6f)) return false;
+    if (prm->retire_by_vote != 0 && prm->retire_by_vote != 1) return false;
+    kp->k_ms = prm->k_multisection;
+    kp->max_sec = prm->max_section_iters;
+    kp->max_halley = prm->max_halley_iters;
+    kp->sec_eps = prm->section_rel_eps;
+    kp->stop_c = prm->stop_c;
+    kp->defl_c = prm->deflation_tol_scale;
+    kp->retire = prm->retire_by_vote;
+    return true;
+}
+
 bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
                        const bed_params* p, bed_counters* counters, cudaStream_t stream)
 {
     if (n < 1 || n > kMaxN) return BED_ERR_UNSUPPORTED_N;
     if (batch < 0) return BED_ERR_INVALID_ARG;
     bed_params prm;
-    bed_default_params(&prm);
-    if (p) prm = *p;
-    if (prm.leaf_size != 1 && prm.leaf_size != 2) return BED_ERR_INVALID_ARG;
-    if (prm.k_multisection < 2 || prm.k_multisection > 64) return BED_ERR_INVALID_ARG;
-    if (prm.max_section_iters < 0 || prm.max_section_iters > 256) return BED_ERR_INVALID_ARG;
-    if (prm.max_halley_iters < 1 || prm.max_halley_iters > 256) return BED_ERR_INVALID_ARG;
-    if (!(prm.section_rel_eps > 0.f && prm.section_rel_eps < 1.f)) return BED_ERR_INVALID_ARG;
-    if (!(prm.stop_c >= 1.f && prm.stop_c <= 1e6f)) return BED_ERR_INVALID_ARG;
-    if (!(prm.deflation_tol_scale >= 1.f && prm.deflation_tol_scale <= 1e6f)) return BED_ERR_INVALID_ARG;
-    if (prm.retire_by_vote != 0 && prm.retire_by_vote != 1) return BED_ERR_INVALID_ARG;
+    KParams kp;
+    if (!make_kparams(p, &prm, &kp)) return BED_ERR_INVALID_ARG;
     const int nmax = n <= 16 ? 16 : (n <= 32 ? 32 : 64);
     int g = 4;
     if (prm.threads_per_matrix != 0) {
@@ -129,14 +144,6 @@ bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_
     if (A == V) return BED_ERR_INVALID_ARG;
     Plan P;
     if (!build_plan(n, prm.leaf_size, &P)) return BED_ERR_INVALID_ARG;
-    KParams kp;
-    kp.k_ms = prm.k_multisection;
-    kp.max_sec = prm.max_section_iters;
-    kp.max_halley = prm.max_halley_iters;
-    kp.sec_eps = prm.section_rel_eps;
-    kp.stop_c = prm.stop_c;
-    kp.defl_c = prm.deflation_tol_scale;
-    kp.retire = prm.retire_by_vote;
     // TMA bulk staging needs a 16-byte aligned source and a size that is a multiple of 16 bytes for
     // every matrix: A 16-byte aligned and n even.
     const bool bulk = ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && (n % 2 == 0);
@@ -145,11 +152,65 @@ bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_
     return BED_OK;
 }
 
+bool tuning_valid(const bed_ragged_tuning& t)
+{
+    for (int n = 1; n <= kMaxN; ++n) {
+        if (t.leaf[n] != 1 && t.leaf[n] != 2) return false;
+        const int tt = t.team[n];
+        if (tt > 3) return false;
+        const int cap = tt == 0 ? 64 : (tt == 1 ? 32 : 16);
+        if (n > cap) return false;
+    }
+    return true;
+}
+
 }  // namespace
 
 }  // namespace bed
 
 extern "C" {
+
+void bed_ragged_default_tuning(bed_ragged_tuning* t)
+{
+    if (!t) return;
+    std::memset(t, 0, sizeof *t);
+    for (int n = 0; n <= bed::kMaxN; ++n) {
+        t->team[n] = static_cast<unsigned char>(n <= 16 ? 2 : (n <= 32 ? 1 : 0));
+        t->leaf[n] = 2;
+    }
+}
+
+size_t bed_eigh_ragged_workspace_size(int64_t count) { return bed::ragged_workspace_bytes(count < 0 ? 0 : count); }
+
+bed_status bed_eigh_ragged_f32(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count,
+                               float* W, const int64_t* w_offsets, float* V, int32_t* info,
+                               const bed_params* p, const bed_ragged_tuning* tuning, void* workspace,
+                               size_t workspace_bytes, bed_counters* counters, cudaStream_t stream)
+{
+    if (count < 0) return BED_ERR_INVALID_ARG;
+    bed_params prm;
+    bed::KParams kp;
+    if (!bed::make_kparams(p, &prm, &kp)) return BED_ERR_INVALID_ARG;
+    bed_ragged_tuning tune;
+    bed_ragged_default_tuning(&tune);
+    if (tuning) tune = *tuning;
+    if (!bed::tuning_valid(tune)) return BED_ERR_INVALID_ARG;
+    if (count == 0) return BED_OK;
+    if (!A || !offsets || !ns || !W || !w_offsets || !V || !workspace) return BED_ERR_INVALID_ARG;
+    const uintptr_t mis4 = (reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(W) |
+                            reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(ns) |
+                            reinterpret_cast<uintptr_t>(info)) & 3u;
+    const uintptr_t mis8 = (reinterpret_cast<uintptr_t>(offsets) | reinterpret_cast<uintptr_t>(w_offsets) |
+                            reinterpret_cast<uintptr_t>(counters)) & 7u;
+    if (mis4 || mis8 || (reinterpret_cast<uintptr_t>(workspace) & 15u)) return BED_ERR_INVALID_ARG;
+    if (A == V) return BED_ERR_INVALID_ARG;
+    if (workspace_bytes < bed::ragged_workspace_bytes(count)) return BED_ERR_INVALID_ARG;
+    if (count > 2147483647LL) return BED_ERR_INVALID_ARG;
+    const cudaError_t e = bed::launch_ragged(A, offsets, ns, count, W, w_offsets, V, info, tune, kp, workspace,
+                                             counters, stream);
+    if (e != cudaSuccess) return bed::cuda_fail(e);
+    return BED_OK;
+}
 
 void bed_default_params(bed_params* p)
 {

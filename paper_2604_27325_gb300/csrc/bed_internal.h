@@ -46,6 +46,11 @@ cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int
                         int64_t batch, const Plan& P, const KParams& kp, bed_counters* counters,
                         bool bulk, cudaStream_t stream);
 
+cudaError_t launch_ragged(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count, float* W,
+                          const int64_t* w_offsets, float* V, int32_t* info, const bed_ragged_tuning& tuning,
+                          const KParams& kp, void* workspace, bed_counters* counters, cudaStream_t stream);
+size_t ragged_workspace_bytes(int64_t count);
+
 template <int NMAX, int G>
 cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int64_t batch,
                           const Plan& P, const KParams& kp, bed_counters* counters, bool bulk,

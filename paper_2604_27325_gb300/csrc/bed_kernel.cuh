@@ -307,22 +307,33 @@ __device__ __forceinline__ RootOut secular_root(const float* __restrict__ d, con
 }
 
 // ---------------------------------------------------------------------------------------------
-// The kernel
+// One matrix, solved by a team of NMAX * G threads (tid = index within the team) that synchronizes
+// on named barrier bar_id. `bar` is the team's mbarrier (initialized by the caller) and `phase` its
+// current phase bit. Returns false only when the staging copy timed out (the caller then stops).
 // ---------------------------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ void team_sync(int bar_id)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "n"(NT) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
 template <int NMAX, int G>
-__global__ void __launch_bounds__(NMAX * G, 65536 / (NMAX * G * 64))
-    eigh_kernel(const float* __restrict__ A, float* __restrict__ W, float* __restrict__ V,
-                int32_t* __restrict__ info, int64_t batch, const __grid_constant__ Plan plan,
-                const KParams kp, bed_counters* __restrict__ counters, int bulk)
+__device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan, const KParams& kp, const int tid,
+                                             const int bar_id, const uint32_t bar, uint32_t& phase,
+                                             const float* __restrict__ Ab, float* __restrict__ Wb,
+                                             float* __restrict__ Vb, int32_t* __restrict__ info_b,
+                                             bed_counters* __restrict__ counters, const bool bulk)
 {
     constexpr int NT = NMAX * G;
     constexpr int NW = NT / 32;
     constexpr int LD = Smem<NMAX, G>::LD;
     constexpr int RPT = NMAX / G;  // rows per thread in the column layout
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<NMAX, G>& S = *reinterpret_cast<Smem<NMAX, G>*>(smem_raw);
-
-    const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const int col = tid % NMAX;
@@ -330,633 +341,643 @@ __global__ void __launch_bounds__(NMAX * G, 65536 / (NMAX * G * 64))
     const int pos = tid / G;
     const int sub = tid % G;
     const int n = plan.n;
-    const uint32_t bar = smem_u32(&S.mbar);
-    uint32_t phase = 0;
 
-    if (bulk) {
-        if (tid == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        __syncthreads();
+    // ---------------- a0: stage the matrix -------------------------------------------------
+    if (bulk) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) {
+        S.info = 0;
+        S.evals = 0;
+        S.roots = 0;
+        S.deflated = 0;
     }
-
-    for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
-        const float* Ab = A + b * (int64_t)n * n;
-        float* Wb = W + b * (int64_t)n;
-        float* Vb = V + b * (int64_t)n * n;
-
-        // ---------------- a0: stage the matrix -------------------------------------------------
-        if (bulk) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    team_sync<NT>(bar_id);
+    bool timed_out = false;
+    if (bulk) {
+        const uint32_t bytes = static_cast<uint32_t>(n * n * sizeof(float));
         if (tid == 0) {
-            S.info = 0;
-            S.evals = 0;
-            S.roots = 0;
-            S.deflated = 0;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(S.M)),
+                "l"(Ab), "r"(bytes), "r"(bar)
+                : "memory");
         }
-        __syncthreads();
-        bool timed_out = false;
-        if (bulk) {
-            const uint32_t bytes = static_cast<uint32_t>(n * n * sizeof(float));
-            if (tid == 0) {
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                             : "memory");
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(S.M)),
-                    "l"(Ab), "r"(bytes), "r"(bar)
-                    : "memory");
+        if (!mbar_wait_bounded(bar, phase, 2000000000ull)) {
+            timed_out = true;
+            // wait once more, again bounded, for the copy still in flight
+            mbar_wait_bounded(bar, phase, 2000000000ull);
+        }
+        phase ^= 1u;
+    } else {
+        for (int i = tid; i < n * n; i += NT) S.M[i] = __ldg(Ab + i);
+    }
+    if (timed_out) atomicOr(&S.info, BED_INFO_TIMEOUT);
+    team_sync<NT>(bar_id);
+
+    // lower triangle -> max |a|, finiteness
+    float amax = 0.f;
+    bool bad = false;
+    for (int i = warp; i < n; i += NW)
+        for (int j = lane; j <= i; j += 32) {
+            const float x = S.M[i * n + j];
+            if (!(fabsf(x) <= FLT_MAX)) bad = true;
+            else amax = fmaxf(amax, fabsf(x));
+        }
+    amax = warp_max(amax);
+    if (lane == 0) S.red[warp] = amax;
+    if (bad) atomicOr(&S.info, BED_INFO_NONFINITE);
+    team_sync<NT>(bar_id);
+    if (S.info & (BED_INFO_NONFINITE | BED_INFO_TIMEOUT)) {
+        const float qnan = __int_as_float(0x7fc00000);
+        for (int i = tid; i < n; i += NT) Wb[i] = qnan;
+        for (int i = tid; i < n * n; i += NT) Vb[i] = qnan;
+        if (info_b && tid == 0) *info_b = S.info;
+        const bool stop = (S.info & BED_INFO_TIMEOUT) != 0;
+        team_sync<NT>(bar_id);
+        return !stop;  // after a timeout the barrier phase is no longer known: the caller stops
+    }
+    amax = S.red[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) amax = fmaxf(amax, S.red[w]);
+    // exact power-of-two scaling to max|a| in [0.5, 1): norms below cannot overflow or underflow
+    int ex = 0;
+    if (amax > 0.f) frexpf(amax, &ex);
+    const float scale = ldexpf(1.f, -ex);
+    const float unscale = ldexpf(1.f, ex);
+    for (int i = warp; i < n; i += NW)
+        for (int j = lane; j <= i; j += 32) {
+            const float x = S.M[i * n + j] * scale;
+            S.A[i * LD + j] = x;
+            S.A[j * LD + i] = x;
+        }
+    team_sync<NT>(bar_id);
+
+    // ---------------- a1: Householder tridiagonalization ------------------------------------
+    for (int k = 0; k + 2 < n; ++k) {
+        const int r0 = k + 1;
+        const int m = n - r0;
+        // every warp forms reflector k from row k (= column k; the matrix is kept symmetric)
+        const float alpha = S.A[k * LD + r0];
+        float part = 0.f;
+        for (int j = r0 + 1 + lane; j < n; j += 32) {
+            const float x = S.A[k * LD + j];
+            part = fmaf(x, x, part);
+        }
+        const float xn2 = warp_sum(part);
+        float tau = 0.f, beta = alpha, scal = 0.f;
+        if (xn2 > 0.f) {
+            const float nrm = sqrtf(fmaf(alpha, alpha, xn2));
+            beta = (alpha >= 0.f) ? -nrm : nrm;
+            tau = (beta - alpha) / beta;
+            scal = 1.f / (alpha - beta);
+        }
+        // p = tau A22 v with v = [1, scal x]: p_i = tau (A[r0][i] + scal sum_{j>r0} A[j][i] x_j).
+        // G lanes per row i, each over interleaved runs of 8 columns j (the runs of the G lanes of
+        // 32/G consecutive rows fall in distinct banks)
+        {
+            float acc = 0.f;
+            const int i = r0 + pos;
+            if (pos < m) {
+#pragma unroll
+                for (int blk = 0; blk < (NMAX + 8 * G - 1) / (8 * G); ++blk)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = r0 + 1 + 8 * (sub + G * blk) + u;
+                        if (j < n) acc = fmaf(S.A[j * LD + i], S.A[k * LD + j], acc);
+                    }
             }
-            if (!mbar_wait_bounded(bar, phase, 2000000000ull)) {
-                timed_out = true;
-                // wait once more, again bounded, for the copy still in flight
-                mbar_wait_bounded(bar, phase, 2000000000ull);
+            acc = gsum<G>(acc);
+            if (pos < m && sub == 0) {
+                S.pp[i] = tau * fmaf(scal, acc, S.A[r0 * LD + i]);
+                S.vv[i] = (i == r0) ? 1.f : S.A[k * LD + i] * scal;
             }
-            phase ^= 1u;
+        }
+        if (tid == 0) {
+            S.d[k] = S.A[k * LD + k];
+            S.e[k] = beta;
+            S.tau[k] = tau;
+        }
+        team_sync<NT>(bar_id);
+        // w = p - (tau/2)(p.v) v (every warp forms p.v); A22 -= v w^T + w v^T; row k keeps v
+        {
+            float pvp = 0.f;
+            for (int i = r0 + lane; i < n; i += 32) pvp = fmaf(S.pp[i], S.vv[i], pvp);
+            const float c = 0.5f * tau * warp_sum(pvp);
+            if (col < m) {
+                const int j = r0 + col;
+                const float vj = S.vv[j];
+                const float wj = fmaf(-c, vj, S.pp[j]);
+                for (int i = r0 + grp; i < n; i += G) {
+                    const float vi = S.vv[i];
+                    const float wi = fmaf(-c, vi, S.pp[i]);
+                    S.A[i * LD + j] -= fmaf(vi, wj, wi * vj);
+                }
+                if (grp == 0 && j > r0) S.A[k * LD + j] = vj;
+            }
+        }
+        team_sync<NT>(bar_id);
+    }
+    if (tid == 0) {
+        if (n >= 2) {
+            S.d[n - 2] = S.A[(n - 2) * LD + n - 2];
+            S.d[n - 1] = S.A[(n - 1) * LD + n - 1];
+            S.e[n - 2] = S.A[(n - 1) * LD + n - 2];
         } else {
-            for (int i = tid; i < n * n; i += NT) S.M[i] = __ldg(Ab + i);
+            S.d[0] = S.A[0];
         }
-        if (timed_out) atomicOr(&S.info, BED_INFO_TIMEOUT);
-        __syncthreads();
+    }
+    team_sync<NT>(bar_id);
 
-        // lower triangle -> max |a|, finiteness
-        float amax = 0.f;
-        bool bad = false;
-        for (int i = warp; i < n; i += NW)
-            for (int j = lane; j <= i; j += 32) {
-                const float x = S.M[i * n + j];
-                if (!(fabsf(x) <= FLT_MAX)) bad = true;
-                else amax = fmaxf(amax, fabsf(x));
-            }
-        amax = warp_max(amax);
-        if (lane == 0) S.red[warp] = amax;
-        if (bad) atomicOr(&S.info, BED_INFO_NONFINITE);
-        __syncthreads();
-        if (S.info & (BED_INFO_NONFINITE | BED_INFO_TIMEOUT)) {
-            const float qnan = __int_as_float(0x7fc00000);
-            for (int i = tid; i < n; i += NT) Wb[i] = qnan;
-            for (int i = tid; i < n * n; i += NT) Vb[i] = qnan;
-            if (info && tid == 0) info[b] = S.info;
-            const bool stop = (S.info & BED_INFO_TIMEOUT) != 0;
-            __syncthreads();
-            if (stop) return;  // the barrier phase is no longer known: leave the remaining matrices
-            continue;
-        }
-        amax = S.red[0];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) amax = fmaxf(amax, S.red[w]);
-        // exact power-of-two scaling to max|a| in [0.5, 1): norms below cannot overflow or underflow
-        int ex = 0;
-        if (amax > 0.f) frexpf(amax, &ex);
-        const float scale = ldexpf(1.f, -ex);
-        const float unscale = ldexpf(1.f, ex);
-        for (int i = warp; i < n; i += NW)
-            for (int j = lane; j <= i; j += 32) {
-                const float x = S.M[i * n + j] * scale;
-                S.A[i * LD + j] = x;
-                S.A[j * LD + i] = x;
-            }
-        __syncthreads();
+    // ---------------- a2: tear (Eq. (3)) ----------------------------------------------------
+    if (tid < n) {
+        float dt = S.d[tid];
+        if ((plan.cut_mask >> tid) & 1ull) dt -= fabsf(S.e[tid]);
+        if (tid > 0 && ((plan.cut_mask >> (tid - 1)) & 1ull)) dt -= fabsf(S.e[tid - 1]);
+        S.d[tid] = dt;
+    }
+    team_sync<NT>(bar_id);
 
-        // ---------------- a1: Householder tridiagonalization ------------------------------------
-        for (int k = 0; k + 2 < n; ++k) {
-            const int r0 = k + 1;
-            const int m = n - r0;
-            // every warp forms reflector k from row k (= column k; the matrix is kept symmetric)
-            const float alpha = S.A[k * LD + r0];
-            float part = 0.f;
-            for (int j = r0 + 1 + lane; j < n; j += 32) {
-                const float x = S.A[k * LD + j];
-                part = fmaf(x, x, part);
+    // ---------------- a3: leaves ------------------------------------------------------------
+    if (tid < plan.nleaves) {
+        const int lo = plan.leaf_lo[tid];
+        if (plan.leaf_hi[tid] - lo == 1) {
+            S.lam[lo] = S.d[lo];
+            S.Q[lo * LD + lo] = 1.f;
+        } else {
+            const float a = S.d[lo], bb = S.e[lo], c = S.d[lo + 1];
+            float t = 0.f;
+            if (bb != 0.f) {
+                const float th = (c - a) / (2.f * bb);
+                t = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
             }
-            const float xn2 = warp_sum(part);
-            float tau = 0.f, beta = alpha, scal = 0.f;
-            if (xn2 > 0.f) {
-                const float nrm = sqrtf(fmaf(alpha, alpha, xn2));
-                beta = (alpha >= 0.f) ? -nrm : nrm;
-                tau = (beta - alpha) / beta;
-                scal = 1.f / (alpha - beta);
-            }
-            // p = tau A22 v with v = [1, scal x]: p_i = tau (A[r0][i] + scal sum_{j>r0} A[j][i] x_j).
-            // G lanes per row i, each over interleaved runs of 8 columns j (the runs of the G lanes of
-            // 32/G consecutive rows fall in distinct banks)
-            {
-                float acc = 0.f;
-                const int i = r0 + pos;
-                if (pos < m) {
-#pragma unroll
-                    for (int blk = 0; blk < (NMAX + 8 * G - 1) / (8 * G); ++blk)
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const int j = r0 + 1 + 8 * (sub + G * blk) + u;
-                            if (j < n) acc = fmaf(S.A[j * LD + i], S.A[k * LD + j], acc);
-                        }
-                }
-                acc = gsum<G>(acc);
-                if (pos < m && sub == 0) {
-                    S.pp[i] = tau * fmaf(scal, acc, S.A[r0 * LD + i]);
-                    S.vv[i] = (i == r0) ? 1.f : S.A[k * LD + i] * scal;
-                }
-            }
-            if (tid == 0) {
-                S.d[k] = S.A[k * LD + k];
-                S.e[k] = beta;
-                S.tau[k] = tau;
-            }
-            __syncthreads();
-            // w = p - (tau/2)(p.v) v (every warp forms p.v); A22 -= v w^T + w v^T; row k keeps v
-            {
-                float pvp = 0.f;
-                for (int i = r0 + lane; i < n; i += 32) pvp = fmaf(S.pp[i], S.vv[i], pvp);
-                const float c = 0.5f * tau * warp_sum(pvp);
-                if (col < m) {
-                    const int j = r0 + col;
-                    const float vj = S.vv[j];
-                    const float wj = fmaf(-c, vj, S.pp[j]);
-                    for (int i = r0 + grp; i < n; i += G) {
-                        const float vi = S.vv[i];
-                        const float wi = fmaf(-c, vi, S.pp[i]);
-                        S.A[i * LD + j] -= fmaf(vi, wj, wi * vj);
-                    }
-                    if (grp == 0 && j > r0) S.A[k * LD + j] = vj;
-                }
-            }
-            __syncthreads();
+            const float cs = rsqrtf(fmaf(t, t, 1.f));
+            const float sn = t * cs;
+            S.lam[lo] = fmaf(-t, bb, a);
+            S.lam[lo + 1] = fmaf(t, bb, c);
+            S.Q[lo * LD + lo] = cs;
+            S.Q[lo * LD + lo + 1] = sn;
+            S.Q[(lo + 1) * LD + lo] = -sn;
+            S.Q[(lo + 1) * LD + lo + 1] = cs;
         }
-        if (tid == 0) {
-            if (n >= 2) {
-                S.d[n - 2] = S.A[(n - 2) * LD + n - 2];
-                S.d[n - 1] = S.A[(n - 1) * LD + n - 1];
-                S.e[n - 2] = S.A[(n - 1) * LD + n - 2];
-            } else {
-                S.d[0] = S.A[0];
-            }
-        }
-        __syncthreads();
+    }
+    team_sync<NT>(bar_id);
 
-        // ---------------- a2: tear (Eq. (3)) ----------------------------------------------------
-        if (tid < n) {
-            float dt = S.d[tid];
-            if ((plan.cut_mask >> tid) & 1ull) dt -= fabsf(S.e[tid]);
-            if (tid > 0 && ((plan.cut_mask >> (tid - 1)) & 1ull)) dt -= fabsf(S.e[tid - 1]);
-            S.d[tid] = dt;
+    // ---------------- a4-a7: merges, deepest level first -----------------------------------
+    for (int L = 0; L < plan.nlevels; ++L) {
+        const int l0 = plan.level_start[L];
+        // position layout: this group's row/column/root t = pos belongs to merge bi
+        const int bi = (pos < n) ? plan.blk[L][pos] : 0xFF;
+        const bool act = (bi != 0xFF);
+        const int lb = bi - l0;  // merge index within the level
+        int lo = 0, mid = 0, hi = 0;
+        if (act) {
+            lo = plan.m_lo[bi];
+            mid = plan.m_mid[bi];
+            hi = plan.m_hi[bi];
         }
-        __syncthreads();
-
-        // ---------------- a3: leaves ------------------------------------------------------------
-        if (tid < plan.nleaves) {
-            const int lo = plan.leaf_lo[tid];
-            if (plan.leaf_hi[tid] - lo == 1) {
-                S.lam[lo] = S.d[lo];
-                S.Q[lo * LD + lo] = 1.f;
-            } else {
-                const float a = S.d[lo], bb = S.e[lo], c = S.d[lo + 1];
-                float t = 0.f;
-                if (bb != 0.f) {
-                    const float th = (c - a) / (2.f * bb);
-                    t = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
-                }
-                const float cs = rsqrtf(fmaf(t, t, 1.f));
-                const float sn = t * cs;
-                S.lam[lo] = fmaf(-t, bb, a);
-                S.lam[lo + 1] = fmaf(t, bb, c);
-                S.Q[lo * LD + lo] = cs;
-                S.Q[lo * LD + lo + 1] = sn;
-                S.Q[(lo + 1) * LD + lo] = -sn;
-                S.Q[(lo + 1) * LD + lo + 1] = cs;
-            }
-        }
-        __syncthreads();
-
-        // ---------------- a4-a7: merges, deepest level first -----------------------------------
-        for (int L = 0; L < plan.nlevels; ++L) {
-            const int l0 = plan.level_start[L];
-            // position layout: this group's row/column/root t = pos belongs to merge bi
-            const int bi = (pos < n) ? plan.blk[L][pos] : 0xFF;
-            const bool act = (bi != 0xFF);
-            const int lb = bi - l0;  // merge index within the level
-            int lo = 0, mid = 0, hi = 0;
+        // P1: z (Eq. (5)), pole order, block scalars
+        {
+            const int c = pos;
+            float zc = 0.f, kc = 0.f;
+            int p = 0;
+            float nz2 = 0.f, dmax = 0.f;
             if (act) {
-                lo = plan.m_lo[bi];
-                mid = plan.m_mid[bi];
-                hi = plan.m_hi[bi];
-            }
-            // P1: z (Eq. (5)), pole order, block scalars
-            {
-                const int c = pos;
-                float zc = 0.f, kc = 0.f;
-                int p = 0;
-                float nz2 = 0.f, dmax = 0.f;
-                if (act) {
-                    const float sig = (S.e[mid - 1] >= 0.f) ? 1.f : -1.f;
-                    const float* z1 = &S.Q[(mid - 1) * LD];  // last row of Q1
-                    const float* z2 = &S.Q[mid * LD];        // first row of Q2
-                    zc = (c < mid) ? sig * z1[c] : z2[c];
-                    kc = sort_key(S.lam[c]);
-                    for (int c2 = lo + sub; c2 < hi; c2 += G) {
-                        const float l2 = S.lam[c2];
-                        const float k2 = sort_key(l2);
-                        p += (k2 < kc) || (k2 == kc && c2 < c);
-                        const float zz = (c2 < mid) ? z1[c2] : z2[c2];
-                        nz2 = fmaf(zz, zz, nz2);
-                        dmax = fmaxf(dmax, fabsf(l2));
-                    }
-                }
-                p = gsumi<G>(p);
-                nz2 = gsum<G>(nz2);
-                dmax = gmax<G>(dmax);
-                if (act && sub == 0) {
-                    S.rank[c] = lo + p;
-                    S.ds[lo + p] = S.lam[c];
-                    S.zs[lo + p] = zc;
-                    if (c == lo) {
-                        const float rho = fabsf(S.e[mid - 1]);
-                        const float bscale = fmaxf(dmax, rho * nz2);
-                        int bex = 0;
-                        if (bscale > 0.f) frexpf(bscale, &bex);
-                        S.brho[lb] = rho;
-                        S.bnz[lb] = sqrtf(nz2);
-                        S.btol[lb] = kp.defl_c * kU * bscale;
-                        S.bsc[lb] = ldexpf(1.f, -bex);
-                        S.brot[lb] = 0;
-                    }
+                const float sig = (S.e[mid - 1] >= 0.f) ? 1.f : -1.f;
+                const float* z1 = &S.Q[(mid - 1) * LD];  // last row of Q1
+                const float* z2 = &S.Q[mid * LD];        // first row of Q2
+                zc = (c < mid) ? sig * z1[c] : z2[c];
+                kc = sort_key(S.lam[c]);
+                for (int c2 = lo + sub; c2 < hi; c2 += G) {
+                    const float l2 = S.lam[c2];
+                    const float k2 = sort_key(l2);
+                    p += (k2 < kc) || (k2 == kc && c2 < c);
+                    const float zz = (c2 < mid) ? z1[c2] : z2[c2];
+                    nz2 = fmaf(zz, zz, nz2);
+                    dmax = fmaxf(dmax, fabsf(l2));
                 }
             }
-            if (tid == 0) S.flag_rot = 0;
-            __syncthreads();
-            // P2: deflation of negligible couplings; detect close-pole pairs
+            p = gsumi<G>(p);
+            nz2 = gsum<G>(nz2);
+            dmax = gmax<G>(dmax);
             if (act && sub == 0) {
-                const int t = pos;
-                const float rho = S.brho[lb], nz = S.bnz[lb], tol = S.btol[lb];
-                const float zp = S.zs[t];
-                const int dfl = (rho * fabsf(zp) * nz <= tol);
-                S.defl[t] = dfl;
-                S.rotj[t] = -1;
-                if (!dfl) {
-                    int j = t + 1;
-                    while (j < hi && rho * fabsf(S.zs[j]) * nz <= tol) ++j;
-                    if (j < hi) {
-                        const float zj = S.zs[j];
-                        const float r = hypotf(zp, zj);
-                        const float cc = zj / r, ss = zp / r;
-                        if (fabsf((S.ds[j] - S.ds[t]) * cc * ss) <= tol) {
-                            S.brot[lb] = 1;
-                            S.flag_rot = 1;
-                        }
+                S.rank[c] = lo + p;
+                S.ds[lo + p] = S.lam[c];
+                S.zs[lo + p] = zc;
+                if (c == lo) {
+                    const float rho = fabsf(S.e[mid - 1]);
+                    const float bscale = fmaxf(dmax, rho * nz2);
+                    int bex = 0;
+                    if (bscale > 0.f) frexpf(bscale, &bex);
+                    S.brho[lb] = rho;
+                    S.bnz[lb] = sqrtf(nz2);
+                    S.btol[lb] = kp.defl_c * kU * bscale;
+                    S.bsc[lb] = ldexpf(1.f, -bex);
+                    S.brot[lb] = 0;
+                }
+            }
+        }
+        if (tid == 0) S.flag_rot = 0;
+        team_sync<NT>(bar_id);
+        // P2: deflation of negligible couplings; detect close-pole pairs
+        if (act && sub == 0) {
+            const int t = pos;
+            const float rho = S.brho[lb], nz = S.bnz[lb], tol = S.btol[lb];
+            const float zp = S.zs[t];
+            const int dfl = (rho * fabsf(zp) * nz <= tol);
+            S.defl[t] = dfl;
+            S.rotj[t] = -1;
+            if (!dfl) {
+                int j = t + 1;
+                while (j < hi && rho * fabsf(S.zs[j]) * nz <= tol) ++j;
+                if (j < hi) {
+                    const float zj = S.zs[j];
+                    const float r = hypotf(zp, zj);
+                    const float cc = zj / r, ss = zp / r;
+                    if (fabsf((S.ds[j] - S.ds[t]) * cc * ss) <= tol) {
+                        S.brot[lb] = 1;
+                        S.flag_rot = 1;
                     }
                 }
             }
-            __syncthreads();
-            // P3: close-pole Givens deflation, one pass in pole order (rare)
-            if (S.flag_rot) {
-                if (act && sub == 0 && pos == lo && S.brot[lb]) {
-                    const float tol = S.btol[lb];
-                    int pj = -1;
-                    for (int p = lo; p < hi; ++p) {
-                        if (S.defl[p]) continue;
-                        if (pj < 0) {
-                            pj = p;
-                            continue;
-                        }
-                        const float r = hypotf(S.zs[pj], S.zs[p]);
-                        const float cc = S.zs[p] / r, ss = S.zs[pj] / r;
-                        if (fabsf((S.ds[p] - S.ds[pj]) * cc * ss) <= tol) {
-                            const float a = S.ds[pj], bb = S.ds[p];
-                            S.ds[pj] = fmaf(cc * cc, a, ss * ss * bb);
-                            S.ds[p] = fmaf(ss * ss, a, cc * cc * bb);
-                            S.zs[p] = r;
-                            S.zs[pj] = 0.f;
-                            S.defl[pj] = 1;
-                            S.rotj[pj] = p;
-                            S.rc[pj] = cc;
-                            S.rs[pj] = ss;
-                        }
+        }
+        team_sync<NT>(bar_id);
+        // P3: close-pole Givens deflation, one pass in pole order (rare)
+        if (S.flag_rot) {
+            if (act && sub == 0 && pos == lo && S.brot[lb]) {
+                const float tol = S.btol[lb];
+                int pj = -1;
+                for (int p = lo; p < hi; ++p) {
+                    if (S.defl[p]) continue;
+                    if (pj < 0) {
                         pj = p;
+                        continue;
                     }
-                }
-                __syncthreads();
-            }
-            // P4: compaction, non-deflated poles first (ascending). The secular problem of the block is
-            // scaled exactly by a power of two to unit size: the derivatives of f grow like
-            // 1/(d - lambda)^3 and would overflow FP32 for blocks whose spectrum is far below 1
-            {
-                const int t = pos;
-                int nb = 0, K = 0;
-                if (act)
-                    for (int p = lo + sub; p < hi; p += G) {
-                        const int nd = !S.defl[p];
-                        K += nd;
-                        nb += (p < t) & nd;
+                    const float r = hypotf(S.zs[pj], S.zs[p]);
+                    const float cc = S.zs[p] / r, ss = S.zs[pj] / r;
+                    if (fabsf((S.ds[p] - S.ds[pj]) * cc * ss) <= tol) {
+                        const float a = S.ds[pj], bb = S.ds[p];
+                        S.ds[pj] = fmaf(cc * cc, a, ss * ss * bb);
+                        S.ds[p] = fmaf(ss * ss, a, cc * cc * bb);
+                        S.zs[p] = r;
+                        S.zs[pj] = 0.f;
+                        S.defl[pj] = 1;
+                        S.rotj[pj] = p;
+                        S.rc[pj] = cc;
+                        S.rs[pj] = ss;
                     }
-                nb = gsumi<G>(nb);
-                K = gsumi<G>(K);
-                if (act && sub == 0) {
-                    const int q = S.defl[t] ? (K + (t - lo - nb)) : nb;
-                    S.inv[lo + q] = t;
-                    S.cd[lo + q] = S.ds[t] * S.bsc[lb];
-                    S.cz[lo + q] = S.zs[t];
-                    S.cz2[lo + q] = S.zs[t] * S.zs[t];
-                    if (t == lo) {
-                        S.bK[lb] = K;
-                        atomicAdd(&S.deflated, static_cast<unsigned>(hi - lo - K));
-                    }
+                    pj = p;
                 }
             }
-            __syncthreads();
-            // P5: secular roots, G lanes per root
-            {
-                int K = 0, q = 0;
-                float sc = 1.f, rho = 0.f;
-                if (act) {
-                    K = S.bK[lb];
-                    q = pos - lo;
-                    sc = S.bsc[lb];
-                    rho = S.brho[lb] * sc;
+            team_sync<NT>(bar_id);
+        }
+        // P4: compaction, non-deflated poles first (ascending). The secular problem of the block is
+        // scaled exactly by a power of two to unit size: the derivatives of f grow like
+        // 1/(d - lambda)^3 and would overflow FP32 for blocks whose spectrum is far below 1
+        {
+            const int t = pos;
+            int nb = 0, K = 0;
+            if (act)
+                for (int p = lo + sub; p < hi; p += G) {
+                    const int nd = !S.defl[p];
+                    K += nd;
+                    nb += (p < t) & nd;
                 }
-                const bool part = act && (q < K);
-                const RootOut r = secular_root<G>(S.cd + lo, S.cz2 + lo, K, q, rho, kp, part, sub);
-                if (sub == 0) {
-                    if (part) {
-                        S.org[lo + q] = lo + r.org;
-                        S.tq[lo + q] = r.tau;
-                        S.lam[lo + q] = (S.cd[lo + r.org] + r.tau) * (1.f / sc);
-                        atomicAdd(&S.evals, static_cast<unsigned>(r.evals));
-                        atomicAdd(&S.roots, 1u);
-                        if (!r.conv) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
-                    } else if (act) {
-                        S.org[lo + q] = lo + q;
-                        S.tq[lo + q] = 0.f;
-                        S.lam[lo + q] = S.cd[lo + q] * (1.f / sc);
+            nb = gsumi<G>(nb);
+            K = gsumi<G>(K);
+            if (act && sub == 0) {
+                const int q = S.defl[t] ? (K + (t - lo - nb)) : nb;
+                S.inv[lo + q] = t;
+                S.cd[lo + q] = S.ds[t] * S.bsc[lb];
+                S.cz[lo + q] = S.zs[t];
+                S.cz2[lo + q] = S.zs[t] * S.zs[t];
+                if (t == lo) {
+                    S.bK[lb] = K;
+                    atomicAdd(&S.deflated, static_cast<unsigned>(hi - lo - K));
+                }
+            }
+        }
+        team_sync<NT>(bar_id);
+        // P5: secular roots, G lanes per root
+        {
+            int K = 0, q = 0;
+            float sc = 1.f, rho = 0.f;
+            if (act) {
+                K = S.bK[lb];
+                q = pos - lo;
+                sc = S.bsc[lb];
+                rho = S.brho[lb] * sc;
+            }
+            const bool part = act && (q < K);
+            const RootOut r = secular_root<G>(S.cd + lo, S.cz2 + lo, K, q, rho, kp, part, sub);
+            if (sub == 0) {
+                if (part) {
+                    S.org[lo + q] = lo + r.org;
+                    S.tq[lo + q] = r.tau;
+                    S.lam[lo + q] = (S.cd[lo + r.org] + r.tau) * (1.f / sc);
+                    atomicAdd(&S.evals, static_cast<unsigned>(r.evals));
+                    atomicAdd(&S.roots, 1u);
+                    if (!r.conv) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
+                } else if (act) {
+                    S.org[lo + q] = lo + q;
+                    S.tq[lo + q] = 0.f;
+                    S.lam[lo + q] = S.cd[lo + q] * (1.f / sc);
+                }
+            }
+        }
+        team_sync<NT>(bar_id);
+        // P6: Gu-Eisenstat z-hat, Eq. (25), as a product of interlaced ratios, each in (0, 1):
+        //   (lambda_{K-1} - d_i)/rho * prod_{j<i} (lambda_j - d_i)/(d_j - d_i)
+        //                            * prod_{i<=j<K-1} (lambda_j - d_i)/(d_{j+1} - d_i)
+        {
+            int K = 0;
+            if (act) K = S.bK[lb];
+            const int i = pos - lo;
+            const bool own = act && (i < K);
+            float prod = 1.f;
+            if (own) {
+                const float di = S.cd[lo + i];
+                if (sub == 0)
+                    prod = ((S.cd[S.org[lo + K - 1]] - di) + S.tq[lo + K - 1]) / (S.brho[lb] * S.bsc[lb]);
+                for (int j = sub; j < K - 1; j += G) {
+                    const float num = (S.cd[S.org[lo + j]] - di) + S.tq[lo + j];  // lambda_j - d_i
+                    const float den = (j < i) ? (S.cd[lo + j] - di) : (S.cd[lo + j + 1] - di);
+                    prod *= num / den;
+                }
+            }
+            prod = gprod<G>(prod);
+            if (own && sub == 0) S.zh[lo + i] = copysignf(sqrtf(fmaxf(prod, 0.f)), S.cz[lo + i]);
+        }
+        team_sync<NT>(bar_id);
+        // P7: eigenvectors of the merge (Eq. (24)) in sorted-pole rows, rotations undone
+        {
+            int K = 0;
+            if (act) K = S.bK[lb];
+            const int q = pos - lo;
+            const int cq = pos;
+            float nrm2 = 0.f;
+            if (act) {
+                if (q < K) {
+                    const float dorg = S.cd[S.org[lo + q]];
+                    const float tq = S.tq[lo + q];
+                    for (int i = sub; i < K; i += G) {
+                        const float v = __fdividef(S.zh[lo + i], (S.cd[lo + i] - dorg) - tq);
+                        S.M[S.inv[lo + i] * LD + cq] = v;
+                        nrm2 = fmaf(v, v, nrm2);
+                    }
+                    for (int p = lo + sub; p < hi; p += G)
+                        if (S.defl[p]) S.M[p * LD + cq] = 0.f;
+                } else {
+                    const int tgt = S.inv[lo + q];
+                    for (int p = lo + sub; p < hi; p += G) S.M[p * LD + cq] = (p == tgt) ? 1.f : 0.f;
+                }
+            }
+            nrm2 = gsum<G>(nrm2);
+            if (act && q < K) {
+                const float inv = rsqrtf(nrm2);
+                for (int i = sub; i < K; i += G) S.M[S.inv[lo + i] * LD + cq] *= inv;
+            }
+            __syncwarp();
+            if (act && sub == 0 && S.brot[lb]) {
+                for (int p = hi - 1; p >= lo; --p) {
+                    const int j = S.rotj[p];
+                    if (j >= 0) {
+                        const float cc = S.rc[p], ss = S.rs[p];
+                        const float yp = S.M[p * LD + cq], yj = S.M[j * LD + cq];
+                        S.M[p * LD + cq] = fmaf(cc, yp, ss * yj);
+                        S.M[j * LD + cq] = fmaf(-ss, yp, cc * yj);
                     }
                 }
             }
-            __syncthreads();
-            // P6: Gu-Eisenstat z-hat, Eq. (25), as a product of interlaced ratios, each in (0, 1):
-            //   (lambda_{K-1} - d_i)/rho * prod_{j<i} (lambda_j - d_i)/(d_j - d_i)
-            //                            * prod_{i<=j<K-1} (lambda_j - d_i)/(d_{j+1} - d_i)
-            {
-                int K = 0;
-                if (act) K = S.bK[lb];
-                const int i = pos - lo;
-                const bool own = act && (i < K);
-                float prod = 1.f;
-                if (own) {
-                    const float di = S.cd[lo + i];
-                    if (sub == 0)
-                        prod = ((S.cd[S.org[lo + K - 1]] - di) + S.tq[lo + K - 1]) / (S.brho[lb] * S.bsc[lb]);
-                    for (int j = sub; j < K - 1; j += G) {
-                        const float num = (S.cd[S.org[lo + j]] - di) + S.tq[lo + j];  // lambda_j - d_i
-                        const float den = (j < i) ? (S.cd[lo + j] - di) : (S.cd[lo + j + 1] - di);
-                        prod *= num / den;
-                    }
-                }
-                prod = gprod<G>(prod);
-                if (own && sub == 0) S.zh[lo + i] = copysignf(sqrtf(fmaxf(prod, 0.f)), S.cz[lo + i]);
-            }
-            __syncthreads();
-            // P7: eigenvectors of the merge (Eq. (24)) in sorted-pole rows, rotations undone
-            {
-                int K = 0;
-                if (act) K = S.bK[lb];
-                const int q = pos - lo;
-                const int cq = pos;
-                float nrm2 = 0.f;
-                if (act) {
-                    if (q < K) {
-                        const float dorg = S.cd[S.org[lo + q]];
-                        const float tq = S.tq[lo + q];
-                        for (int i = sub; i < K; i += G) {
-                            const float v = __fdividef(S.zh[lo + i], (S.cd[lo + i] - dorg) - tq);
-                            S.M[S.inv[lo + i] * LD + cq] = v;
-                            nrm2 = fmaf(v, v, nrm2);
-                        }
-                        for (int p = lo + sub; p < hi; p += G)
-                            if (S.defl[p]) S.M[p * LD + cq] = 0.f;
-                    } else {
-                        const int tgt = S.inv[lo + q];
-                        for (int p = lo + sub; p < hi; p += G) S.M[p * LD + cq] = (p == tgt) ? 1.f : 0.f;
-                    }
-                }
-                nrm2 = gsum<G>(nrm2);
-                if (act && q < K) {
-                    const float inv = rsqrtf(nrm2);
-                    for (int i = sub; i < K; i += G) S.M[S.inv[lo + i] * LD + cq] *= inv;
-                }
-                __syncwarp();
-                if (act && sub == 0 && S.brot[lb]) {
-                    for (int p = hi - 1; p >= lo; --p) {
-                        const int j = S.rotj[p];
-                        if (j >= 0) {
-                            const float cc = S.rc[p], ss = S.rs[p];
-                            const float yp = S.M[p * LD + cq], yj = S.M[j * LD + cq];
-                            S.M[p * LD + cq] = fmaf(cc, yp, ss * yj);
-                            S.M[j * LD + cq] = fmaf(-ss, yp, cc * yj);
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            // P8: Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)); rows of Q^ are gathered through the pole order
-            {
-                const int bc = (col < n) ? plan.blk[L][col] : 0xFF;
-                float acc[RPT];
-                int clo = 0, cmid = 0, chi = 0;
-                if (bc != 0xFF) {
-                    clo = plan.m_lo[bc];
-                    cmid = plan.m_mid[bc];
-                    chi = plan.m_hi[bc];
+        }
+        team_sync<NT>(bar_id);
+        // P8: Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)); rows of Q^ are gathered through the pole order
+        {
+            const int bc = (col < n) ? plan.blk[L][col] : 0xFF;
+            float acc[RPT];
+            int clo = 0, cmid = 0, chi = 0;
+            if (bc != 0xFF) {
+                clo = plan.m_lo[bc];
+                cmid = plan.m_mid[bc];
+                chi = plan.m_hi[bc];
 #pragma unroll
-                    for (int k = 0; k < RPT; ++k) acc[k] = 0.f;
-                    for (int c = clo; c < chi; ++c) {
-                        const float mv = S.M[S.rank[c] * LD + col];
-                        const bool left = c < cmid;
-#pragma unroll
-                        for (int k = 0; k < RPT; ++k) {
-                            const int r = clo + grp + G * k;
-                            if (r < chi && ((r < cmid) == left)) acc[k] = fmaf(S.Q[r * LD + c], mv, acc[k]);
-                        }
-                    }
-                }
-                __syncthreads();
-                if (bc != 0xFF) {
+                for (int k = 0; k < RPT; ++k) acc[k] = 0.f;
+                for (int c = clo; c < chi; ++c) {
+                    const float mv = S.M[S.rank[c] * LD + col];
+                    const bool left = c < cmid;
 #pragma unroll
                     for (int k = 0; k < RPT; ++k) {
                         const int r = clo + grp + G * k;
-                        if (r < chi) S.Q[r * LD + col] = acc[k];
+                        if (r < chi && ((r < cmid) == left)) acc[k] = fmaf(S.Q[r * LD + c], mv, acc[k]);
                     }
                 }
             }
-            __syncthreads();
-        }
-
-        // ---------------- a8: back-transform V = H_0 ... H_{n-3} Q_T ----------------------------
-        // Blocks of kBT reflectors: H_{k0} ... H_{k0+b-1} = I - Y T Y^T with T upper triangular
-        // (forward accumulation); Y[i][r] = v_{k0+r}[i] is 0 above row k0+r+1, 1 on it and row k0+r
-        // of A below it. Blocks are applied last to first: Q <- Q - Y (T (Y^T Q)).
-        if (n >= 3) {
-            const int nr = n - 2;
-            const int ngr = (nr + kBT - 1) / kBT;
-            float* Tm = S.M;                    // ngr blocks of kBT x kBT: T above the diagonal, Gram below
-            float* W1 = S.M + ngr * kBT * kBT;  // kBT x NMAX
-            for (int g = warp; g < ngr; g += NW) {
-                const int k0 = g * kBT;
-                const int bsz = min(kBT, nr - k0);
-                float* T = Tm + g * kBT * kBT;
-                // Gram entries Y[:, r]^T Y[:, j] for r < j, one pair per lane, stored at T[j][r]
-                int p = lane, r = 0;
-                while (r < kBT - 1 && p >= kBT - 1 - r) {
-                    p -= kBT - 1 - r;
-                    ++r;
+            team_sync<NT>(bar_id);
+            if (bc != 0xFF) {
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    const int r = clo + grp + G * k;
+                    if (r < chi) S.Q[r * LD + col] = acc[k];
                 }
-                const int j = r + 1 + p;
-                if (r < kBT - 1 && j < bsz) {
-                    const int kr = k0 + r, kj = k0 + j;
-                    float s = S.A[kr * LD + kj + 1];  // Y[kj+1][r] times Y[kj+1][j] = 1
-                    for (int i = kj + 2; i < n; ++i) s = fmaf(S.A[kr * LD + i], S.A[kj * LD + i], s);
-                    T[j * kBT + r] = s;
+            }
+        }
+        team_sync<NT>(bar_id);
+    }
+
+    // ---------------- a8: back-transform V = H_0 ... H_{n-3} Q_T ----------------------------
+    // Blocks of kBT reflectors: H_{k0} ... H_{k0+b-1} = I - Y T Y^T with T upper triangular
+    // (forward accumulation); Y[i][r] = v_{k0+r}[i] is 0 above row k0+r+1, 1 on it and row k0+r
+    // of A below it. Blocks are applied last to first: Q <- Q - Y (T (Y^T Q)).
+    if (n >= 3) {
+        const int nr = n - 2;
+        const int ngr = (nr + kBT - 1) / kBT;
+        float* Tm = S.M;                    // ngr blocks of kBT x kBT: T above the diagonal, Gram below
+        float* W1 = S.M + ngr * kBT * kBT;  // kBT x NMAX
+        for (int g = warp; g < ngr; g += NW) {
+            const int k0 = g * kBT;
+            const int bsz = min(kBT, nr - k0);
+            float* T = Tm + g * kBT * kBT;
+            // Gram entries Y[:, r]^T Y[:, j] for r < j, one pair per lane, stored at T[j][r]
+            int p = lane, r = 0;
+            while (r < kBT - 1 && p >= kBT - 1 - r) {
+                p -= kBT - 1 - r;
+                ++r;
+            }
+            const int j = r + 1 + p;
+            if (r < kBT - 1 && j < bsz) {
+                const int kr = k0 + r, kj = k0 + j;
+                float s = S.A[kr * LD + kj + 1];  // Y[kj+1][r] times Y[kj+1][j] = 1
+                for (int i = kj + 2; i < n; ++i) s = fmaf(S.A[kr * LD + i], S.A[kj * LD + i], s);
+                T[j * kBT + r] = s;
+            }
+            __syncwarp();
+            // T[jj][jj] = tau_jj; T[0:jj, jj] = T[0:jj, 0:jj] w with w_s = -tau_jj Gram[s][jj]
+            for (int jj = 0; jj < bsz; ++jj) {
+                const float tj = S.tau[k0 + jj];
+                const float w = (lane < jj) ? -tj * T[jj * kBT + lane] : 0.f;
+                float acc = 0.f;
+                for (int s2 = 0; s2 < jj; ++s2) {
+                    const float ws = __shfl_sync(kFull, w, s2);
+                    if (lane <= s2) acc = fmaf(T[lane * kBT + s2], ws, acc);
                 }
                 __syncwarp();
-                // T[jj][jj] = tau_jj; T[0:jj, jj] = T[0:jj, 0:jj] w with w_s = -tau_jj Gram[s][jj]
-                for (int jj = 0; jj < bsz; ++jj) {
-                    const float tj = S.tau[k0 + jj];
-                    const float w = (lane < jj) ? -tj * T[jj * kBT + lane] : 0.f;
-                    float acc = 0.f;
-                    for (int s2 = 0; s2 < jj; ++s2) {
-                        const float ws = __shfl_sync(kFull, w, s2);
-                        if (lane <= s2) acc = fmaf(T[lane * kBT + s2], ws, acc);
-                    }
-                    __syncwarp();
-                    if (lane < jj) T[lane * kBT + jj] = acc;
-                    if (lane == jj) T[jj * kBT + jj] = tj;
-                    __syncwarp();
-                }
+                if (lane < jj) T[lane * kBT + jj] = acc;
+                if (lane == jj) T[jj * kBT + jj] = tj;
+                __syncwarp();
             }
-            __syncthreads();
-            for (int g = ngr - 1; g >= 0; --g) {
-                const int k0 = g * kBT;
-                const int bsz = min(kBT, nr - k0);
-                const float* T = Tm + g * kBT * kBT;
-                // W1 = Y^T Q (bsz x n): this thread's rows r = grp + G*rr of W1, one pass over Q's column;
-                // rows i <= k0 + kBT hold the unit and zero entries of Y, the rows below are plain
-                constexpr int RB = (kBT + G - 1) / G;
-                if (col < n) {
-                    float acc[RB];
+        }
+        team_sync<NT>(bar_id);
+        for (int g = ngr - 1; g >= 0; --g) {
+            const int k0 = g * kBT;
+            const int bsz = min(kBT, nr - k0);
+            const float* T = Tm + g * kBT * kBT;
+            // W1 = Y^T Q (bsz x n): this thread's rows r = grp + G*rr of W1, one pass over Q's column;
+            // rows i <= k0 + kBT hold the unit and zero entries of Y, the rows below are plain
+            constexpr int RB = (kBT + G - 1) / G;
+            if (col < n) {
+                float acc[RB];
 #pragma unroll
-                    for (int rr = 0; rr < RB; ++rr) acc[rr] = 0.f;
-                    const int iedge = min(k0 + kBT, n - 1);
-                    for (int i = k0 + 1; i <= iedge; ++i) {
-                        const float qv = S.Q[i * LD + col];
-#pragma unroll
-                        for (int rr = 0; rr < RB; ++rr) {
-                            const int kr = k0 + grp + G * rr;
-                            const float y = (i > kr + 1) ? S.A[kr * LD + i] : ((i == kr + 1) ? 1.f : 0.f);
-                            acc[rr] = fmaf(y, qv, acc[rr]);
-                        }
-                    }
-                    for (int i = iedge + 1; i < n; ++i) {
-                        const float qv = S.Q[i * LD + col];
-#pragma unroll
-                        for (int rr = 0; rr < RB; ++rr)
-                            acc[rr] = fmaf(S.A[(k0 + grp + G * rr) * LD + i], qv, acc[rr]);
-                    }
+                for (int rr = 0; rr < RB; ++rr) acc[rr] = 0.f;
+                const int iedge = min(k0 + kBT, n - 1);
+                for (int i = k0 + 1; i <= iedge; ++i) {
+                    const float qv = S.Q[i * LD + col];
 #pragma unroll
                     for (int rr = 0; rr < RB; ++rr) {
-                        const int r = grp + G * rr;
-                        if (r < bsz) W1[r * NMAX + col] = acc[rr];
+                        const int kr = k0 + grp + G * rr;
+                        const float y = (i > kr + 1) ? S.A[kr * LD + i] : ((i == kr + 1) ? 1.f : 0.f);
+                        acc[rr] = fmaf(y, qv, acc[rr]);
                     }
                 }
-                __syncthreads();
-                // Q -= Y (T W1)
-                if (col < n) {
-                    float w2[kBT];
+                for (int i = iedge + 1; i < n; ++i) {
+                    const float qv = S.Q[i * LD + col];
+#pragma unroll
+                    for (int rr = 0; rr < RB; ++rr)
+                        acc[rr] = fmaf(S.A[(k0 + grp + G * rr) * LD + i], qv, acc[rr]);
+                }
+#pragma unroll
+                for (int rr = 0; rr < RB; ++rr) {
+                    const int r = grp + G * rr;
+                    if (r < bsz) W1[r * NMAX + col] = acc[rr];
+                }
+            }
+            team_sync<NT>(bar_id);
+            // Q -= Y (T W1)
+            if (col < n) {
+                float w2[kBT];
+#pragma unroll
+                for (int r = 0; r < kBT; ++r) {
+                    float s = 0.f;
+                    if (r < bsz)
+                        for (int s2 = r; s2 < bsz; ++s2) s = fmaf(T[r * kBT + s2], W1[s2 * NMAX + col], s);
+                    w2[r] = s;
+                }
+                // rows k0+r of A with r >= bsz are not reflectors (possibly never written): skip them
+                int i = k0 + 1 + grp;
+                for (; i <= k0 + kBT && i < n; i += G) {
+                    float acc = S.Q[i * LD + col];
 #pragma unroll
                     for (int r = 0; r < kBT; ++r) {
-                        float s = 0.f;
-                        if (r < bsz)
-                            for (int s2 = r; s2 < bsz; ++s2) s = fmaf(T[r * kBT + s2], W1[s2 * NMAX + col], s);
-                        w2[r] = s;
-                    }
-                    // rows k0+r of A with r >= bsz are not reflectors (possibly never written): skip them
-                    int i = k0 + 1 + grp;
-                    for (; i <= k0 + kBT && i < n; i += G) {
-                        float acc = S.Q[i * LD + col];
-#pragma unroll
-                        for (int r = 0; r < kBT; ++r) {
-                            const int kr = k0 + r;
-                            if (r < bsz) {
-                                const float y = (i > kr + 1) ? S.A[kr * LD + i] : ((i == kr + 1) ? 1.f : 0.f);
-                                acc = fmaf(-y, w2[r], acc);
-                            }
+                        const int kr = k0 + r;
+                        if (r < bsz) {
+                            const float y = (i > kr + 1) ? S.A[kr * LD + i] : ((i == kr + 1) ? 1.f : 0.f);
+                            acc = fmaf(-y, w2[r], acc);
                         }
-                        S.Q[i * LD + col] = acc;
                     }
-                    for (; i < n; i += G) {
-                        float acc = S.Q[i * LD + col];
-#pragma unroll
-                        for (int r = 0; r < kBT; ++r)
-                            if (r < bsz) acc = fmaf(-S.A[(k0 + r) * LD + i], w2[r], acc);
-                        S.Q[i * LD + col] = acc;
-                    }
+                    S.Q[i * LD + col] = acc;
                 }
-                __syncthreads();
+                for (; i < n; i += G) {
+                    float acc = S.Q[i * LD + col];
+#pragma unroll
+                    for (int r = 0; r < kBT; ++r)
+                        if (r < bsz) acc = fmaf(-S.A[(k0 + r) * LD + i], w2[r], acc);
+                    S.Q[i * LD + col] = acc;
+                }
             }
+            team_sync<NT>(bar_id);
         }
+    }
 
-        // ---------------- a9: ascending order, signs, store ------------------------------------
-        {
-            int r = 0;
-            if (pos < n) {
-                const float kc = sort_key(S.lam[pos]);
-                for (int t2 = sub; t2 < n; t2 += G) {
-                    const float k2 = sort_key(S.lam[t2]);
-                    r += (k2 < kc) || (k2 == kc && t2 < pos);
-                }
+    // ---------------- a9: ascending order, signs, store ------------------------------------
+    {
+        int r = 0;
+        if (pos < n) {
+            const float kc = sort_key(S.lam[pos]);
+            for (int t2 = sub; t2 < n; t2 += G) {
+                const float k2 = sort_key(S.lam[t2]);
+                r += (k2 < kc) || (k2 == kc && t2 < pos);
             }
-            r = gsumi<G>(r);
-            if (pos < n && sub == 0) S.outc[r] = pos;
         }
-        __syncthreads();
-        {
-            int src = 0;
-            float vm = -1.f;
-            int im = 0;
-            if (pos < n) {
-                src = S.outc[pos];
-                for (int i = sub; i < n; i += G) {
-                    const float v = fabsf(S.Q[i * LD + src]);
-                    if (v > vm) {
-                        vm = v;
-                        im = i;
-                    }
+        r = gsumi<G>(r);
+        if (pos < n && sub == 0) S.outc[r] = pos;
+    }
+    team_sync<NT>(bar_id);
+    {
+        int src = 0;
+        float vm = -1.f;
+        int im = 0;
+        if (pos < n) {
+            src = S.outc[pos];
+            for (int i = sub; i < n; i += G) {
+                const float v = fabsf(S.Q[i * LD + src]);
+                if (v > vm) {
+                    vm = v;
+                    im = i;
                 }
             }
+        }
 #pragma unroll
-            for (int o = G / 2; o; o >>= 1) {
-                const float v2 = __shfl_xor_sync(kFull, vm, o);
-                const int i2 = __shfl_xor_sync(kFull, im, o);
-                if (v2 > vm || (v2 == vm && i2 < im)) {
-                    vm = v2;
-                    im = i2;
-                }
-            }
-            if (pos < n && sub == 0) {
-                S.sgn[pos] = (S.Q[im * LD + src] < 0.f) ? -1.f : 1.f;
-                Wb[pos] = S.lam[src] * unscale;
+        for (int o = G / 2; o; o >>= 1) {
+            const float v2 = __shfl_xor_sync(kFull, vm, o);
+            const int i2 = __shfl_xor_sync(kFull, im, o);
+            if (v2 > vm || (v2 == vm && i2 < im)) {
+                vm = v2;
+                im = i2;
             }
         }
-        __syncthreads();
-        for (int i = warp; i < n; i += NW)
-            for (int j = lane; j < n; j += 32) Vb[i * n + j] = S.sgn[j] * S.Q[i * LD + S.outc[j]];
-        if (tid == 0) {
-            if (info) info[b] = S.info;
-            if (counters) {
-                atomicAdd(&counters->matrices, 1ull);
-                atomicAdd(&counters->roots, static_cast<unsigned long long>(S.roots));
-                atomicAdd(&counters->evals, static_cast<unsigned long long>(S.evals));
-                atomicAdd(&counters->deflated, static_cast<unsigned long long>(S.deflated));
-            }
+        if (pos < n && sub == 0) {
+            S.sgn[pos] = (S.Q[im * LD + src] < 0.f) ? -1.f : 1.f;
+            Wb[pos] = S.lam[src] * unscale;
         }
+    }
+    team_sync<NT>(bar_id);
+    for (int i = warp; i < n; i += NW)
+        for (int j = lane; j < n; j += 32) Vb[i * n + j] = S.sgn[j] * S.Q[i * LD + S.outc[j]];
+    if (tid == 0) {
+        if (info_b) *info_b = S.info;
+        if (counters) {
+            atomicAdd(&counters->matrices, 1ull);
+            atomicAdd(&counters->roots, static_cast<unsigned long long>(S.roots));
+            atomicAdd(&counters->evals, static_cast<unsigned long long>(S.evals));
+            atomicAdd(&counters->deflated, static_cast<unsigned long long>(S.deflated));
+        }
+    }
+    team_sync<NT>(bar_id);
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Uniform-size kernel: one team = one thread block, matrices b = blockIdx.x, blockIdx.x + gridDim.x, ...
+// ---------------------------------------------------------------------------------------------
+template <int NMAX, int G>
+__global__ void __launch_bounds__(NMAX * G, 65536 / (NMAX * G * 64))
+    eigh_kernel(const float* __restrict__ A, float* __restrict__ W, float* __restrict__ V,
+                int32_t* __restrict__ info, int64_t batch, const __grid_constant__ Plan plan,
+                const KParams kp, bed_counters* __restrict__ counters, int bulk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<NMAX, G>& S = *reinterpret_cast<Smem<NMAX, G>*>(smem_raw);
+    const int n = plan.n;
+    const uint32_t bar = smem_u32(&S.mbar);
+    uint32_t phase = 0;
+    if (bulk) {
+        if (threadIdx.x == 0) mbar_init(bar);
         __syncthreads();
+    }
+    for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
+        if (!solve_matrix<NMAX, G>(S, plan, kp, threadIdx.x, 0, bar, phase, A + b * (int64_t)n * n,
+                                   W + b * (int64_t)n, V + b * (int64_t)n * n, info ? info + b : nullptr,
+                                   counters, bulk != 0))
+            return;
     }
 }
 

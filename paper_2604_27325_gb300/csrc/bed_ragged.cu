@@ -1,0 +1,240 @@
+// Ragged batches: one persistent launch over matrices of mixed n (1 <= n <= 64).
+//
+// Every thread block has 256 threads and works through "units" taken from an atomic counter in the
+// caller's workspace. A unit is one team configuration and up to as many matrices as it has teams:
+//   team type 0: one team of 256 threads (the n <= 64 code path: NMAX 64, 4 lanes per row)
+//   team type 1: two teams of 128 threads (NMAX 32, 4 lanes per row)
+//   team type 2: four teams of 64 threads (NMAX 16, 4 lanes per row)
+//   team type 3: eight teams of 32 threads (NMAX 16, 2 lanes per row)
+// Each team runs the same per-matrix code as the uniform launch (solve_matrix) on its own slice of
+// shared memory, with its own named barrier and mbarrier. A one-block pre-kernel sorts the matrices by
+// (team type, n descending) into the workspace so that the costliest units are handed out first, and
+// resets the counter; both launches are stream-ordered and can be captured into a CUDA graph.
+#include <cstring>
+#include <mutex>
+
+#include "bed_kernel.cuh"
+
+namespace bed {
+
+constexpr int kRaggedThreads = 256;
+constexpr int kTeamTypes = 4;
+constexpr int kMaxTeams = 8;
+
+__host__ __device__ constexpr int team_count(int t) { return t == 0 ? 1 : (t == 1 ? 2 : (t == 2 ? 4 : 8)); }
+__host__ __device__ constexpr int team_nmax(int t) { return t == 0 ? 64 : (t == 1 ? 32 : 16); }
+
+template <int NMAX, int G>
+__host__ __device__ constexpr size_t slice_bytes()
+{
+    return (sizeof(Smem<NMAX, G>) + 15) / 16 * 16;
+}
+
+__host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kRaggedSmem = cmax(cmax(slice_bytes<64, 4>(), 2 * slice_bytes<32, 4>()),
+                                    cmax(4 * slice_bytes<16, 4>(), 8 * slice_bytes<16, 2>()));
+
+// Divide trees for every n and both leaf sizes, written once per device (setup before first use).
+__device__ Plan g_plans[2][kMaxN + 1];
+
+struct RaggedHeader {
+    unsigned int next_unit;                   // work counter (reset by the pre-kernel)
+    unsigned int total_units;
+    unsigned int unit_start[kTeamTypes + 1];  // first unit of each team type
+    unsigned int mat_start[kTeamTypes + 1];   // first position in `order` of each team type
+    unsigned int pad[4];
+};
+static_assert(sizeof(RaggedHeader) == 64, "workspace header is 64 bytes");
+
+struct RaggedTune {
+    uint8_t team[kMaxN + 1];
+    uint8_t leaf[kMaxN + 1];
+};
+
+// Orders the matrices by (team type, n descending) with a counting sort; invalid sizes are flagged.
+__global__ void __launch_bounds__(1024) ragged_order_kernel(const int32_t* __restrict__ ns, int64_t count,
+                                                            const RaggedTune tune, RaggedHeader* __restrict__ hdr,
+                                                            int32_t* __restrict__ order, int32_t* __restrict__ info)
+{
+    constexpr int NK = kTeamTypes * kMaxN;  // key = type * 64 + (64 - n)
+    __shared__ unsigned int hist[NK];
+    __shared__ unsigned int offs[NK];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < NK; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int64_t i = tid; i < count; i += blockDim.x) {
+        const int n = ns[i];
+        if (n < 1 || n > kMaxN) {
+            if (info) info[i] = BED_INFO_BAD_N;
+            continue;
+        }
+        atomicAdd(&hist[tune.team[n] * kMaxN + (kMaxN - n)], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned int acc = 0, units = 0;
+        for (int t = 0; t < kTeamTypes; ++t) {
+            hdr->mat_start[t] = acc;
+            hdr->unit_start[t] = units;
+            unsigned int ct = 0;
+            for (int k = 0; k < kMaxN; ++k) {
+                offs[t * kMaxN + k] = acc + ct;
+                ct += hist[t * kMaxN + k];
+            }
+            acc += ct;
+            units += (ct + team_count(t) - 1) / team_count(t);
+        }
+        hdr->mat_start[kTeamTypes] = acc;
+        hdr->unit_start[kTeamTypes] = units;
+        hdr->total_units = units;
+        hdr->next_unit = 0;
+    }
+    __syncthreads();
+    for (int64_t i = tid; i < count; i += blockDim.x) {
+        const int n = ns[i];
+        if (n < 1 || n > kMaxN) continue;
+        const unsigned int p = atomicAdd(&offs[tune.team[n] * kMaxN + (kMaxN - n)], 1u);
+        order[p] = static_cast<int32_t>(i);
+    }
+}
+
+struct RaggedArgs {
+    const float* A;
+    const int64_t* offsets;
+    const int32_t* ns;
+    float* W;
+    const int64_t* w_offsets;
+    float* V;
+    int32_t* info;
+    RaggedHeader* hdr;
+    const int32_t* order;
+    bed_counters* counters;
+};
+
+template <int NMAX, int G>
+__device__ __forceinline__ bool run_team(unsigned char* smem, const RaggedArgs& a, const RaggedTune& tune,
+                                         const KParams& kp, int team, int ttid, unsigned first, unsigned last,
+                                         unsigned long long* mbars, uint32_t* phases)
+{
+    const unsigned slot = first + team;
+    if (slot >= last) return true;  // the whole team is idle in a partial unit
+    const int i = a.order[slot];
+    const int n = a.ns[i];
+    const Plan& plan = g_plans[tune.leaf[n] - 1][n];
+    Smem<NMAX, G>& S = *reinterpret_cast<Smem<NMAX, G>*>(smem + team * slice_bytes<NMAX, G>());
+    const float* Ab = a.A + a.offsets[i];
+    const bool bulk = (n % 2 == 0) && ((reinterpret_cast<uintptr_t>(Ab) & 15u) == 0);
+    uint32_t phase = phases[team];
+    const bool ok = solve_matrix<NMAX, G>(S, plan, kp, ttid, 1 + team, smem_u32(&mbars[team]), phase, Ab,
+                                          a.W + a.w_offsets[i], a.V + a.offsets[i],
+                                          a.info ? a.info + i : nullptr, a.counters, bulk);
+    if (ttid == 0) phases[team] = phase;
+    return ok;
+}
+
+__global__ void __launch_bounds__(kRaggedThreads, 4)
+    ragged_kernel(const RaggedArgs a, const RaggedTune tune, const KParams kp)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long mbars[kMaxTeams];
+    __shared__ uint32_t phases[kMaxTeams];
+    __shared__ unsigned int s_unit;
+    __shared__ int s_stop;
+    const int tid = threadIdx.x;
+    if (tid < kMaxTeams) {
+        mbar_init(smem_u32(&mbars[tid]));
+        phases[tid] = 0;
+    }
+    if (tid == 0) s_stop = 0;
+    __syncthreads();
+    const unsigned total = a.hdr->total_units;
+    for (;;) {
+        if (tid == 0) s_unit = atomicAdd(&a.hdr->next_unit, 1u);
+        __syncthreads();
+        const unsigned u = s_unit;
+        if (u >= total || s_stop) break;
+        int t = 0;
+        while (t + 1 < kTeamTypes && u >= a.hdr->unit_start[t + 1]) ++t;
+        const unsigned first = a.hdr->mat_start[t] + (u - a.hdr->unit_start[t]) * team_count(t);
+        const unsigned last = a.hdr->mat_start[t + 1];
+        bool ok = true;
+        switch (t) {
+        case 0: ok = run_team<64, 4>(smem_raw, a, tune, kp, 0, tid, first, last, mbars, phases); break;
+        case 1: ok = run_team<32, 4>(smem_raw, a, tune, kp, tid / 128, tid % 128, first, last, mbars, phases); break;
+        case 2: ok = run_team<16, 4>(smem_raw, a, tune, kp, tid / 64, tid % 64, first, last, mbars, phases); break;
+        default: ok = run_team<16, 2>(smem_raw, a, tune, kp, tid / 32, tid % 32, first, last, mbars, phases); break;
+        }
+        if (!ok) s_stop = 1;  // a staging copy timed out: this block stops taking work
+        // the next unit may stage a matrix by bulk copy into memory any thread wrote in this one
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+}
+
+namespace {
+
+std::mutex g_setup_mutex;
+bool g_setup_done[64] = {};
+int g_ragged_grid[64] = {};
+
+// Per-device setup: divide trees for every n into g_plans, shared-memory attribute, grid size.
+cudaError_t ragged_setup(int* grid)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_setup_done[dev]) {
+        static Plan host_plans[2][kMaxN + 1];
+        std::memset(host_plans, 0, sizeof host_plans);
+        for (int leaf = 1; leaf <= 2; ++leaf)
+            for (int n = 1; n <= kMaxN; ++n) build_plan(n, leaf, &host_plans[leaf - 1][n]);
+        e = cudaMemcpyToSymbol(g_plans, host_plans, sizeof host_plans);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(ragged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kRaggedSmem));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(ragged_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ragged_kernel, kRaggedThreads, kRaggedSmem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_ragged_grid[dev] = (per_sm > 0 ? per_sm : 1) * sms;
+        g_setup_done[dev] = true;
+    }
+    *grid = g_ragged_grid[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_ragged(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count, float* W,
+                          const int64_t* w_offsets, float* V, int32_t* info, const bed_ragged_tuning& tuning,
+                          const KParams& kp, void* workspace, bed_counters* counters, cudaStream_t stream)
+{
+    int grid = 0;
+    cudaError_t e = ragged_setup(&grid);
+    if (e != cudaSuccess) return e;
+    RaggedTune tune;
+    std::memcpy(tune.team, tuning.team, sizeof tune.team);
+    std::memcpy(tune.leaf, tuning.leaf, sizeof tune.leaf);
+    RaggedHeader* hdr = static_cast<RaggedHeader*>(workspace);
+    int32_t* order = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) + sizeof(RaggedHeader));
+    ragged_order_kernel<<<1, 1024, 0, stream>>>(ns, count, tune, hdr, order, info);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    RaggedArgs a{A, offsets, ns, W, w_offsets, V, info, hdr, order, counters};
+    ragged_kernel<<<grid, kRaggedThreads, kRaggedSmem, stream>>>(a, tune, kp);
+    return cudaGetLastError();
+}
+
+size_t ragged_workspace_bytes(int64_t count)
+{
+    return (sizeof(RaggedHeader) + static_cast<size_t>(count) * sizeof(int32_t) + 255) / 256 * 256;
+}
+
+}  // namespace bed

@@ -112,3 +112,25 @@ def test_no_cpu_fallback():
         pytest.skip("GPU present")
     with pytest.raises(B.BedError):
         B.batched_eigh(torch.eye(4).unsqueeze(0))
+
+
+def test_ragged_validation_before_launch():
+    ws = B.bed_eigh_ragged_workspace_size(10)
+    assert ws >= 64 + 40 and ws % 256 == 0
+    assert B.bed_eigh_ragged_workspace_size(0) >= 64
+    args = dict(A_ptr=FAKE, offsets_ptr=FAKE, ns_ptr=FAKE, count=10, W_ptr=FAKE, w_offsets_ptr=FAKE,
+                V_ptr=FAKE + 4096, info_ptr=None, params=None, tuning=None, workspace_ptr=FAKE, workspace_bytes=ws)
+    assert B.bed_eigh_ragged_f32(**{**args, "count": 0}) == B.BED_OK
+    assert B.bed_eigh_ragged_f32(**{**args, "count": -1}) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_ragged_f32(**{**args, "workspace_bytes": ws - 1}) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_ragged_f32(**{**args, "workspace_ptr": FAKE + 8}) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_ragged_f32(**{**args, "offsets_ptr": FAKE + 4}) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_ragged_f32(**{**args, "ns_ptr": 0}) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_ragged_f32(**{**args, "V_ptr": FAKE}) == B.BED_ERR_INVALID_ARG
+    t = B.bed_ragged_default_tuning()
+    assert [t.team[n] for n in (1, 16, 17, 32, 33, 64)] == [2, 2, 1, 1, 0, 0]
+    t.team[20] = 2  # a 64-thread team (n <= 16) cannot hold n = 20
+    assert B.bed_eigh_ragged_f32(**{**args, "tuning": t}) == B.BED_ERR_INVALID_ARG
+    t = B.bed_ragged_default_tuning()
+    t.leaf[5] = 3
+    assert B.bed_eigh_ragged_f32(**{**args, "tuning": t}) == B.BED_ERR_INVALID_ARG
