@@ -40,7 +40,8 @@ typedef enum {
     BED_OK = 0,
     BED_ERR_INVALID_ARG = 1,   /* null pointer, negative batch, misaligned pointer, bad params */
     BED_ERR_UNSUPPORTED_N = 2, /* n outside [1, bed_max_n()] */
-    BED_ERR_CUDA = 3           /* the CUDA runtime refused the launch or an attribute call */
+    BED_ERR_CUDA = 3,          /* the CUDA runtime refused the launch or an attribute call */
+    BED_ERR_TOO_LARGE = 4      /* the batch exceeds a fixed capacity (bed_eigh_ragged_f32_noalloc) */
 } bed_status;
 
 /* per-matrix outcome flags written to info[b] */
@@ -151,6 +152,31 @@ bed_status bed_eigh_ragged_f32(const float* A, const int64_t* offsets, const int
                                float* W, const int64_t* w_offsets, float* V, int32_t* info,
                                const bed_params* p, const bed_ragged_tuning* tuning, void* workspace,
                                size_t workspace_bytes, bed_counters* counters, cudaStream_t stream);
+
+/*
+ * Allocation-free variant of bed_eigh_ragged_f32 (the paper has no counterpart; this is a convenience
+ * of this library). Some callers cannot obtain device memory for the workspace: code that runs inside
+ * a host framework whose allocator owns all of the device memory it may use, plugins handed only the
+ * input and output buffers, or services that must not call cudaMalloc once they are running (it may
+ * fail under memory pressure and it synchronizes the device). This entry point takes no workspace:
+ * it uses a scratch array compiled into the library, of fixed size, that every GPU which loads the
+ * library keeps for the life of the process.
+ *   - At most BED_NOALLOC_MAX_COUNT matrices per call; a larger count returns BED_ERR_TOO_LARGE
+ *     before anything is enqueued. The scratch holds BED_NOALLOC_SCRATCH_BYTES bytes.
+ *   - The first call on a device looks up the scratch's device address (and performs the same
+ *     one-time device setup as bed_eigh_ragged_f32); make that first call before any stream capture.
+ *   - Every call on a device uses the same scratch, and it keeps what the last call left there: the
+ *     launches reset everything they read before reading it. Two calls whose work overlaps on the
+ *     GPU (different streams without ordering between them) race on the scratch and give undefined
+ *     results; order such calls or use bed_eigh_ragged_f32 with separate workspaces.
+ *   - It calls no allocation routine. Arguments otherwise as for bed_eigh_ragged_f32.
+ */
+#define BED_NOALLOC_MAX_COUNT 65536
+#define BED_NOALLOC_SCRATCH_BYTES (64 + 4 * BED_NOALLOC_MAX_COUNT)
+bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count,
+                                       float* W, const int64_t* w_offsets, float* V, int32_t* info,
+                                       const bed_params* p, const bed_ragged_tuning* tuning,
+                                       bed_counters* counters, cudaStream_t stream);
 
 /* Largest supported n (64). */
 int bed_max_n(void);

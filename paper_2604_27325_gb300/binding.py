@@ -18,6 +18,8 @@ BED_OK = 0
 BED_ERR_INVALID_ARG = 1
 BED_ERR_UNSUPPORTED_N = 2
 BED_ERR_CUDA = 3
+BED_ERR_TOO_LARGE = 4
+BED_NOALLOC_MAX_COUNT = 65536
 
 BED_INFO_OK = 0
 BED_INFO_NOT_CONVERGED = 1
@@ -58,6 +60,7 @@ EXPORTED = [
     "bed_eigh_f32",
     "bed_eigh_f32_counted",
     "bed_eigh_ragged_f32",
+    "bed_eigh_ragged_f32_noalloc",
     "bed_eigh_ragged_workspace_size",
     "bed_ragged_default_tuning",
     "bed_max_n",
@@ -98,6 +101,9 @@ def lib() -> C.CDLL:
             L.bed_eigh_ragged_f32.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp, C.POINTER(bed_params),
                                               C.POINTER(bed_ragged_tuning), vp, C.c_size_t, vp, vp]
             L.bed_eigh_ragged_f32.restype = C.c_int
+            L.bed_eigh_ragged_f32_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp, C.POINTER(bed_params),
+                                                      C.POINTER(bed_ragged_tuning), vp, vp]
+            L.bed_eigh_ragged_f32_noalloc.restype = C.c_int
             _lib = L
         return _lib
 
@@ -143,6 +149,17 @@ def bed_eigh_ragged_f32(A_ptr: int, offsets_ptr: int, ns_ptr: int, count: int, W
                                      C.byref(params) if params is not None else None,
                                      C.byref(tuning) if tuning is not None else None,
                                      workspace_ptr, workspace_bytes, counters_ptr, stream)
+
+
+def bed_eigh_ragged_f32_noalloc(A_ptr: int, offsets_ptr: int, ns_ptr: int, count: int, W_ptr: int,
+                                w_offsets_ptr: int, V_ptr: int, info_ptr: int | None, params: bed_params | None,
+                                tuning: bed_ragged_tuning | None, counters_ptr: int | None = None,
+                                stream: int = 0) -> int:
+    """Raw call of the workspace-free ragged entry point (for callers that cannot allocate device
+    memory): at most BED_NOALLOC_MAX_COUNT matrices; returns the bed_status code."""
+    return lib().bed_eigh_ragged_f32_noalloc(A_ptr, offsets_ptr, ns_ptr, count, W_ptr, w_offsets_ptr, V_ptr,
+                                             info_ptr, C.byref(params) if params is not None else None,
+                                             C.byref(tuning) if tuning is not None else None, counters_ptr, stream)
 
 
 def bed_max_n() -> int:

@@ -240,6 +240,36 @@ bed_status bed_eigh_f32_counted(const float* A, float* W, float* V, int32_t* inf
     return bed::eigh_common(A, W, V, info, batch, n, p, counters, stream);
 }
 
+bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count,
+                                       float* W, const int64_t* w_offsets, float* V, int32_t* info,
+                                       const bed_params* p, const bed_ragged_tuning* tuning,
+                                       bed_counters* counters, cudaStream_t stream)
+{
+    if (count < 0) return BED_ERR_INVALID_ARG;
+    if (count > BED_NOALLOC_MAX_COUNT) return BED_ERR_TOO_LARGE;
+    bed_params prm;
+    bed::KParams kp;
+    if (!bed::make_kparams(p, &prm, &kp)) return BED_ERR_INVALID_ARG;
+    bed_ragged_tuning tune;
+    bed_ragged_default_tuning(&tune);
+    if (tuning) tune = *tuning;
+    if (!bed::tuning_valid(tune)) return BED_ERR_INVALID_ARG;
+    if (count == 0) return BED_OK;
+    if (!A || !offsets || !ns || !W || !w_offsets || !V) return BED_ERR_INVALID_ARG;
+    const uintptr_t mis4 = (reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(W) |
+                            reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(ns) |
+                            reinterpret_cast<uintptr_t>(info)) & 3u;
+    const uintptr_t mis8 = (reinterpret_cast<uintptr_t>(offsets) | reinterpret_cast<uintptr_t>(w_offsets) |
+                            reinterpret_cast<uintptr_t>(counters)) & 7u;
+    if (mis4 || mis8 || A == V) return BED_ERR_INVALID_ARG;
+    void* scratch = nullptr;
+    cudaError_t e = bed::noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return bed::cuda_fail(e);
+    e = bed::launch_ragged(A, offsets, ns, count, W, w_offsets, V, info, tune, kp, scratch, counters, stream);
+    if (e != cudaSuccess) return bed::cuda_fail(e);
+    return BED_OK;
+}
+
 int bed_max_n(void) { return bed::kMaxN; }
 
 const char* bed_status_string(bed_status s)
@@ -249,6 +279,7 @@ const char* bed_status_string(bed_status s)
     case BED_ERR_INVALID_ARG: return "BED_ERR_INVALID_ARG";
     case BED_ERR_UNSUPPORTED_N: return "BED_ERR_UNSUPPORTED_N";
     case BED_ERR_CUDA: return "BED_ERR_CUDA";
+    case BED_ERR_TOO_LARGE: return "BED_ERR_TOO_LARGE";
     }
     return "BED_UNKNOWN_STATUS";
 }

@@ -50,6 +50,8 @@ cudaError_t launch_ragged(const float* A, const int64_t* offsets, const int32_t*
                           const int64_t* w_offsets, float* V, int32_t* info, const bed_ragged_tuning& tuning,
                           const KParams& kp, void* workspace, bed_counters* counters, cudaStream_t stream);
 size_t ragged_workspace_bytes(int64_t count);
+// Device address of the allocation-free entry point's scratch on the current device (looked up once).
+cudaError_t noalloc_scratch(void** ptr);
 
 template <int NMAX, int G>
 cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int64_t batch,

@@ -237,4 +237,33 @@ size_t ragged_workspace_bytes(int64_t count)
     return (sizeof(RaggedHeader) + static_cast<size_t>(count) * sizeof(int32_t) + 255) / 256 * 256;
 }
 
+// Scratch of the allocation-free ragged entry point: the workspace of a batch of at most
+// BED_NOALLOC_MAX_COUNT matrices, as a file-scope device array that every GPU loading the library
+// holds until the process exits. In host code `g_noalloc_scratch` only names the symbol; its device
+// address is looked up once per device below and is what the kernels receive.
+static __device__ __align__(256) unsigned char
+    g_noalloc_scratch[(sizeof(RaggedHeader) + BED_NOALLOC_MAX_COUNT * sizeof(int32_t) + 255) / 256 * 256];
+
+namespace {
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[64] = {};
+}  // namespace
+
+cudaError_t noalloc_scratch(void** ptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // with device `dev` current
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
 }  // namespace bed
