@@ -88,6 +88,8 @@ def lib():
             L.orc_eigh_batch_f32.argtypes = [C.c_int64, C.c_int, C.POINTER(C.c_float), C.POINTER(Opts),
                                              dp, dp, C.c_int, C.POINTER(Stats)]
             L.orc_eigh_batch_f32.restype = C.c_int
+            L.orc_eigh_backward.argtypes = [C.c_int, dp, dp, dp, dp, C.c_double, dp]
+            L.orc_eigh_backward.restype = None
             _lib = L
         return _lib
 
@@ -205,3 +207,16 @@ def eigh_batch_f32(A, nthreads: int | None = None, opts=None):
                                     C.byref(opts) if opts is not None else None,
                                     _dp(W), _dp(V), int(nthreads), C.byref(st))
     return W, V, st, used
+
+
+def eigh_backward(W, V, gW, gV, gap_eps: float = 0.0):
+    """Gradient dL/dA (symmetric) from the eigendecomposition's W, V and the loss gradients gW, gV
+    (either may be None). FP64; one matrix."""
+    W, V = _f64(W), _f64(V)
+    n = W.shape[0]
+    gA = np.zeros((n, n))
+    gW = _f64(gW) if gW is not None else None
+    gV = _f64(gV) if gV is not None else None
+    lib().orc_eigh_backward(n, _dp(W), _dp(V), _dp(gW) if gW is not None else None,
+                            _dp(gV) if gV is not None else None, gap_eps, _dp(gA))
+    return gA

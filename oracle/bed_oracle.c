@@ -679,6 +679,59 @@ void orc_eigh(int n, const double* A, const orc_opts* opts, double* W, double* V
 }
 
 /* ------------------------------------------------------------------------ */
+/* gradient of a loss of (W, V) with respect to A                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Reverse-mode derivative of the eigendecomposition A = V diag(W) V^T (the eigendecomposition layer the
+ * paper's introduction motivates): with first-order perturbation theory,
+ * dW_i = v_i^T dA v_i and dv_i = sum_{j != i} v_j (v_j^T dA v_i)/(W_i - W_j), so for gW = dL/dW and
+ * gV = dL/dV,
+ *     G = V (diag(gW) + F o (V^T gV)) V^T,   F_ij = 1/(W_j - W_i) for i != j, F_ii = 0,
+ * and gA = (G + G^T)/2, the gradient over symmetric perturbations of A. Pairs with
+ * |W_j - W_i| <= gap_eps get F_ij = 0 (their eigenvectors are not determined individually).
+ * gW or gV may be NULL (zero). All n x n arrays row-major, V with eigenvectors in columns.
+ */
+void orc_eigh_backward(int n, const double* W, const double* V, const double* gW, const double* gV,
+                       double gap_eps, double* gA)
+{
+    double* M = (double*)calloc((size_t)n * n, sizeof(double));
+    double* T = (double*)calloc((size_t)n * n, sizeof(double));
+    double* G = (double*)calloc((size_t)n * n, sizeof(double));
+    /* M = diag(gW) + F o (V^T gV) */
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            double m = 0;
+            if (i == j) {
+                m = gW ? gW[i] : 0.0;
+            } else if (gV && fabs(W[j] - W[i]) > gap_eps) {
+                double vg = 0;
+                for (int k = 0; k < n; k++) vg += V[k * n + i] * gV[k * n + j];
+                m = vg / (W[j] - W[i]);
+            }
+            M[i * n + j] = m;
+        }
+    /* G = V M V^T */
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            double acc = 0;
+            for (int k = 0; k < n; k++) acc += V[i * n + k] * M[k * n + j];
+            T[i * n + j] = acc;
+        }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            double acc = 0;
+            for (int k = 0; k < n; k++) acc += T[i * n + k] * V[j * n + k];
+            G[i * n + j] = acc;
+        }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) gA[i * n + j] = 0.5 * (G[i * n + j] + G[j * n + i]);
+    free(M);
+    free(T);
+    free(G);
+}
+
+/* ------------------------------------------------------------------------ */
 /* batch driver (plain threads over independent matrices)                  */
 /* ------------------------------------------------------------------------ */
 

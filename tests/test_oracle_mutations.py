@@ -41,6 +41,8 @@ MUTATIONS = {
     "backtransform_transposed": ("acc += H[r * n + k] * QT[k * n + c];", "acc += H[k * n + r] * QT[k * n + c];"),
     "leaf_rotation_sign": ("    Q[2] = -sn;\n", "    Q[2] = sn;\n"),
     "sign_convention_flipped": ("if (V[im * n + c] < 0)", "if (V[im * n + c] > 0)"),
+    "backward_gap_sign": ("m = vg / (W[j] - W[i]);", "m = vg / (W[i] - W[j]);"),
+    "backward_not_symmetrized": ("gA[i * n + j] = 0.5 * (G[i * n + j] + G[j * n + i]);", "gA[i * n + j] = G[i * n + j];"),
     "deflation_drops_rho": ("defl[p] = (rho * fabs(zz[p]) * nz <= tol);", "defl[p] = (fabs(zz[p]) <= 0.5);"),
 }
 
