@@ -405,6 +405,45 @@ def run_ours(args, rank, world, local):
     if bad:
         raise RuntimeError(f"{bad} matrices of the ragged runs reported a non-zero info")
 
+    # differentiation: forward + hand-written backward on 1024 covariances of size 32 (min gap 1e-3)
+    dA, dw, dG = workloads.differentiation()
+    db, dn, _ = dA.shape
+    dAd = torch.from_numpy(dA).to(dev)
+    dWd, dVd = torch.empty(db, dn, device=dev), torch.empty(db, dn, dn, device=dev)
+    dgW, dgV = torch.from_numpy(dw).to(dev), torch.from_numpy(dG).to(dev)
+    dgA = torch.empty(db, dn, dn, device=dev)
+
+    def diff_step():
+        st = B.bed_eigh_f32(dAd.data_ptr(), dWd.data_ptr(), dVd.data_ptr(), None, db, dn, None, sp)
+        st2 = B.bed_eigh_backward_f32(dWd.data_ptr(), dVd.data_ptr(), dgW.data_ptr(), dgV.data_ptr(),
+                                      dgA.data_ptr(), db, dn, 0.0, sp)
+        if st != B.BED_OK or st2 != B.BED_OK:
+            raise B.BedError("differentiation step failed")
+
+    for _ in range(args.warmup):
+        diff_step()
+    torch.cuda.synchronize(dev)
+    fb_ms, bw_ms = [], []
+    for s_ in range(K):
+        flush.fill_(float(s_))
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        B.bed_eigh_f32(dAd.data_ptr(), dWd.data_ptr(), dVd.data_ptr(), None, db, dn, None, sp)
+        e1.record(stream)
+        B.bed_eigh_backward_f32(dWd.data_ptr(), dVd.data_ptr(), dgW.data_ptr(), dgV.data_ptr(), dgA.data_ptr(),
+                                db, dn, 0.0, sp)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        fb_ms.append(e0.elapsed_time(e2))
+        bw_ms.append(e1.elapsed_time(e2))
+    differentiation = {
+        "workload": "1024 FP32 covariances, n = 32, min eigen-gap >= 1e-3; L = sum w_i lambda_i + <G, V>",
+        "forward_backward": db * world * K / (max_over_ranks(sum(fb_ms), world) / 1e3),
+        "backward_only": db * world * K / (max_over_ranks(sum(bw_ms), world) / 1e3),
+        "unit": "matrices/s",
+        "backward_ms": statistics.mean(bw_ms),
+    }
+
     # end to end through the public API with host buffers
     host = {n: torch.from_numpy(inputs[n]).pin_memory() for n in SIZES}
     for _ in range(max(1, min(args.warmup, 3))):
@@ -434,6 +473,7 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed before every step (512 MB write), flush outside the per-step CUDA events"},
         "paths": {"per_size_launches": value, "ragged_persistent_graph": uniform_via_ragged, "unit": "matrices/s"},
         "ragged": ragged,
+        "differentiation": differentiation,
         "per_n_ms": {str(n): statistics.mean(v) for n, v in per_n_ms.items()},
         "kbar": {str(n): kbar[n] for n in SIZES},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",

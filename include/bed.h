@@ -178,6 +178,19 @@ bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, c
                                        const bed_params* p, const bed_ragged_tuning* tuning,
                                        bed_counters* counters, cudaStream_t stream);
 
+/*
+ * Backward of the eigendecomposition layer (the paper's introduction motivates ED as a differentiable
+ * layer of a network): given the outputs W [batch][n], V [batch][n][n] of bed_eigh_f32 and the
+ * gradients of a loss with respect to them, gW (same shape as W) and gV (same shape as V), writes
+ *     gA = (G + G^T)/2,  G = V (diag(gW) + F o (V^T gV)) V^T,
+ * F_ij = 1/(W_j - W_i) when |W_j - W_i| > gap_eps (i != j) and 0 otherwise (pairs that close are not
+ * separable eigenvectors), into gA [batch][n][n]. gA is the gradient over symmetric perturbations of A
+ * (torch.linalg.eigh's convention). All pointers DEVICE memory; gW or gV may be NULL (zero gradient);
+ * gA may not alias V. gap_eps >= 0 and finite. Same ownership, error and stream rules as bed_eigh_f32.
+ */
+bed_status bed_eigh_backward_f32(const float* W, const float* V, const float* gW, const float* gV, float* gA,
+                                 int64_t batch, int n, float gap_eps, cudaStream_t stream);
+
 /* Largest supported n (64). */
 int bed_max_n(void);
 

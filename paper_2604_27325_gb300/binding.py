@@ -59,6 +59,7 @@ EXPORTED = [
     "bed_default_params",
     "bed_eigh_f32",
     "bed_eigh_f32_counted",
+    "bed_eigh_backward_f32",
     "bed_eigh_ragged_f32",
     "bed_eigh_ragged_f32_noalloc",
     "bed_eigh_ragged_workspace_size",
@@ -94,6 +95,8 @@ def lib() -> C.CDLL:
             L.bed_last_cuda_error.restype = C.c_char_p
             L.bed_plan_describe.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.bed_plan_describe.restype = C.c_int
+            L.bed_eigh_backward_f32.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_int, C.c_float, vp]
+            L.bed_eigh_backward_f32.restype = C.c_int
             L.bed_ragged_default_tuning.argtypes = [C.POINTER(bed_ragged_tuning)]
             L.bed_ragged_default_tuning.restype = None
             L.bed_eigh_ragged_workspace_size.argtypes = [C.c_int64]
@@ -128,6 +131,12 @@ def bed_eigh_f32_counted(A_ptr: int, W_ptr: int, V_ptr: int, info_ptr: int | Non
                          params: bed_params | None, counters_ptr: int, stream: int = 0) -> int:
     return lib().bed_eigh_f32_counted(A_ptr, W_ptr, V_ptr, info_ptr, batch, n,
                                       C.byref(params) if params is not None else None, counters_ptr, stream)
+
+
+def bed_eigh_backward_f32(W_ptr: int, V_ptr: int, gW_ptr: int | None, gV_ptr: int | None, gA_ptr: int, batch: int,
+                          n: int, gap_eps: float = 0.0, stream: int = 0) -> int:
+    """Raw call of the backward kernel: device pointers as integers; returns the bed_status code."""
+    return lib().bed_eigh_backward_f32(W_ptr, V_ptr, gW_ptr, gV_ptr, gA_ptr, batch, n, gap_eps, stream)
 
 
 def bed_ragged_default_tuning() -> bed_ragged_tuning:
@@ -348,3 +357,40 @@ def batched_eigh_ragged(mats, params: bed_params | None = None, tuning: bed_ragg
     rb = RaggedBatch(ns, params=params, tuning=tuning).load(mats).solve()
     res = rb.results()
     return (res, rb.info[: rb.count]) if return_info else res
+
+
+class EighFunction(torch.autograd.Function):
+    """Differentiable batched eigendecomposition: forward by bed_eigh_f32, backward by
+    bed_eigh_backward_f32 (both CUDA kernels of this library)."""
+
+    @staticmethod
+    def forward(ctx, A, params, gap_eps):
+        W, V = batched_eigh(A, params)
+        ctx.save_for_backward(W, V)
+        ctx.gap_eps = float(gap_eps)
+        return W, V
+
+    @staticmethod
+    def backward(ctx, gW, gV):
+        W, V = ctx.saved_tensors
+        n = V.shape[-1]
+        Wc = W.reshape(-1, n).contiguous()
+        Vc = V.reshape(-1, n, n).contiguous()
+        b = Vc.shape[0]
+        gWc = gW.reshape(-1, n).contiguous().float() if gW is not None else None
+        gVc = gV.reshape(-1, n, n).contiguous().float() if gV is not None else None
+        gA = torch.empty_like(Vc)
+        st = bed_eigh_backward_f32(Wc.data_ptr(), Vc.data_ptr(), gWc.data_ptr() if gWc is not None else None,
+                                   gVc.data_ptr() if gVc is not None else None, gA.data_ptr(), b, n, ctx.gap_eps,
+                                   torch.cuda.current_stream(V.device).cuda_stream)
+        _check(st)
+        return gA.reshape(V.shape), None, None
+
+
+def eigh(A: torch.Tensor, params: bed_params | None = None, gap_eps: float = 0.0):
+    """Differentiable ``(W, V) = eigh(A)`` for a CUDA FP32 batch ``A[..., n, n]`` (lower triangle read).
+    The gradient returned for A is symmetric (gradient over symmetric perturbations); eigenvalue pairs
+    closer than ``gap_eps`` do not couple their eigenvectors in the backward pass."""
+    if not A.is_cuda:
+        raise BedError("eigh (differentiable) expects a CUDA tensor")
+    return EighFunction.apply(A, params, gap_eps)

@@ -1,4 +1,5 @@
 // C ABI of the batched eigensolver: argument validation, the divide-tree plan, launch selection.
+#include <cfloat>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -266,6 +267,22 @@ bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, c
     cudaError_t e = bed::noalloc_scratch(&scratch);
     if (e != cudaSuccess) return bed::cuda_fail(e);
     e = bed::launch_ragged(A, offsets, ns, count, W, w_offsets, V, info, tune, kp, scratch, counters, stream);
+    if (e != cudaSuccess) return bed::cuda_fail(e);
+    return BED_OK;
+}
+
+bed_status bed_eigh_backward_f32(const float* W, const float* V, const float* gW, const float* gV, float* gA,
+                                 int64_t batch, int n, float gap_eps, cudaStream_t stream)
+{
+    if (n < 1 || n > bed::kMaxN) return BED_ERR_UNSUPPORTED_N;
+    if (batch < 0 || !(gap_eps >= 0.f && gap_eps <= FLT_MAX)) return BED_ERR_INVALID_ARG;
+    if (batch == 0) return BED_OK;
+    if (!W || !V || !gA || gA == V) return BED_ERR_INVALID_ARG;
+    const uintptr_t mis = (reinterpret_cast<uintptr_t>(W) | reinterpret_cast<uintptr_t>(V) |
+                           reinterpret_cast<uintptr_t>(gW) | reinterpret_cast<uintptr_t>(gV) |
+                           reinterpret_cast<uintptr_t>(gA)) & 3u;
+    if (mis) return BED_ERR_INVALID_ARG;
+    const cudaError_t e = bed::launch_backward(W, V, gW, gV, gA, batch, n, gap_eps, stream);
     if (e != cudaSuccess) return bed::cuda_fail(e);
     return BED_OK;
 }

@@ -50,6 +50,8 @@ cudaError_t launch_ragged(const float* A, const int64_t* offsets, const int32_t*
                           const int64_t* w_offsets, float* V, int32_t* info, const bed_ragged_tuning& tuning,
                           const KParams& kp, void* workspace, bed_counters* counters, cudaStream_t stream);
 size_t ragged_workspace_bytes(int64_t count);
+cudaError_t launch_backward(const float* W, const float* V, const float* gW, const float* gV, float* gA,
+                            int64_t batch, int n, float gap_eps, cudaStream_t stream);
 // Device address of the allocation-free entry point's scratch on the current device (looked up once).
 cudaError_t noalloc_scratch(void** ptr);
 

@@ -78,6 +78,24 @@ def ragged(count: int = 8192, nmin: int = 4, nmax: int = 64, seed: int = SEED_RA
     return mats, ns
 
 
+def differentiation(batch: int = 1024, n: int = 32, seed: int = SEED_DIFF, min_gap: float = 1e-3):
+    """Covariances (as ``covariance``) redrawn until the smallest eigen-gap of the FP32 matrix (LAPACK, FP64)
+    is at least ``min_gap``, plus the loss weights of L = sum_i w_i lambda_i + <G, V>: w ~ N(0,1)^n and
+    G ~ N(0,1)^{n x n} per matrix. Returns (A float32 [b,n,n], w float32 [b,n], G float32 [b,n,n])."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((batch, n, n), np.float32)
+    k = 0
+    while k < batch:
+        X = rng.standard_normal((n, 2 * n))
+        A = _sym32(X @ X.T / (2 * n) + 1e-3 * np.eye(n))
+        if np.diff(np.linalg.eigvalsh(A.astype(np.float64))).min() >= min_gap:
+            out[k] = A
+            k += 1
+    w = rng.standard_normal((batch, n)).astype(np.float32)
+    G = rng.standard_normal((batch, n, n)).astype(np.float32)
+    return out, w, G
+
+
 def special_cases(n: int, seed: int = 7):
     """Degenerate inputs that force every branch: zero, identity, diagonal, repeated eigenvalues,
     a rank-one matrix, a block-diagonal matrix (exact zero couplings), a tridiagonal Toeplitz matrix.
