@@ -444,6 +444,31 @@ def run_ours(args, rank, world, local):
         "backward_ms": statistics.mean(bw_ms),
     }
 
+    # serving: Poisson arrivals, requests of b ~ U{1..256} matrices of one n ~ U{8..64}, 4 GB budget
+    from paper_2604_27325_gb300 import serve
+
+    serving = None
+    if args.serving_seconds > 0:
+        pool = serve.request_pool()
+        keep = ("p50_ms", "p99_ms", "mean_ms", "matrices_per_s", "requests", "offered_requests", "launches",
+                "peak_device_bytes")
+        serving = {
+            "workload": "Poisson arrivals; request = b ~ U{1..256} FP32 matrices of one n ~ U{8..64} (gapped known "
+                        "spectra and covariances); 4 GB device budget; latency = submit to results in host memory",
+            "seconds": args.serving_seconds,
+        }
+        serving["servers"] = ("native request loop (bed_server_*): continuous batching over the ragged "
+                              "kernel on 3 streams vs FIFO with one uniform-size launch per request")
+        for rate in (args.serving_rate, 4 * args.serving_rate):
+            srv = serve.NativeServer(budget_bytes=4 << 30, tuning=tuning)
+            ours_s = serve.run_load_native(srv, rate=rate, seconds=args.serving_seconds, pool=pool)
+            srv.close()
+            q = serve.NativeServer(budget_bytes=4 << 30, mode="fifo")
+            base_s = serve.run_load_native(q, rate=rate, seconds=args.serving_seconds, pool=pool)
+            q.close()
+            serving[f"rate_{rate:.0f}"] = {"continuous_batching": {k: ours_s.get(k) for k in keep},
+                                           "fifo_per_request_launches": {k: base_s.get(k) for k in keep}}
+
     # end to end through the public API with host buffers
     host = {n: torch.from_numpy(inputs[n]).pin_memory() for n in SIZES}
     for _ in range(max(1, min(args.warmup, 3))):
@@ -474,6 +499,7 @@ def run_ours(args, rank, world, local):
         "paths": {"per_size_launches": value, "ragged_persistent_graph": uniform_via_ragged, "unit": "matrices/s"},
         "ragged": ragged,
         "differentiation": differentiation,
+        "serving": serving,
         "per_n_ms": {str(n): statistics.mean(v) for n, v in per_n_ms.items()},
         "kbar": {str(n): kbar[n] for n in SIZES},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -505,6 +531,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=5.0)
+    ap.add_argument("--serving-seconds", type=float, default=8.0)
+    ap.add_argument("--serving-rate", type=float, default=2000.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

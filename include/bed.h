@@ -41,7 +41,8 @@ typedef enum {
     BED_ERR_INVALID_ARG = 1,   /* null pointer, negative batch, misaligned pointer, bad params */
     BED_ERR_UNSUPPORTED_N = 2, /* n outside [1, bed_max_n()] */
     BED_ERR_CUDA = 3,          /* the CUDA runtime refused the launch or an attribute call */
-    BED_ERR_TOO_LARGE = 4      /* the batch exceeds a fixed capacity (bed_eigh_ragged_f32_noalloc) */
+    BED_ERR_TOO_LARGE = 4,     /* the batch exceeds a fixed capacity (bed_eigh_ragged_f32_noalloc, servers) */
+    BED_ERR_TIMEOUT = 5        /* bed_server_wait: the request did not complete in time */
 } bed_status;
 
 /* per-matrix outcome flags written to info[b] */
@@ -190,6 +191,63 @@ bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, c
  */
 bed_status bed_eigh_backward_f32(const float* W, const float* V, const float* gW, const float* gV, float* gA,
                                  int64_t batch, int n, float gap_eps, cudaStream_t stream);
+
+/*
+ * Request loop (continuous batching) for serving eigendecompositions on the current device.
+ * A request is b matrices of one size n in host memory (row-major, lower triangle read). The server
+ * admits requests in arrival order while their device memory (input, eigenvectors, eigenvalues) fits
+ * `device_budget_bytes` and their results fit `host_result_bytes` of pinned host memory; everything
+ * admitted since the previous launch is solved by one ragged launch (bed_eigh_ragged_f32) on a free
+ * one of `streams` streams, so requests that arrive while others run are admitted as memory and
+ * streams free up and their work overlaps on the device. mode 1 instead runs one uniform-size launch
+ * per request, first come first served, on one stream (the plain per-request baseline).
+ * The server allocates its device and pinned host memory once, in bed_server_create, and owns two
+ * threads; every entry point below is thread-safe.
+ */
+typedef struct bed_server bed_server;
+
+typedef struct {
+    size_t device_budget_bytes; /* device arena (default 4 GB) */
+    size_t host_result_bytes;   /* pinned host memory for results held until released (default 2 GB) */
+    int streams;                /* launches that may be in flight at once (default 3; 1 in mode 1) */
+    int max_launch_matrices;    /* cap on the matrices of one launch (default 16384) */
+    int mode;                   /* 0: continuous batching (default); 1: one launch per request */
+} bed_server_config;
+
+typedef struct {
+    int64_t requests, matrices, launches; /* completed since creation or the last reset */
+    int64_t peak_device_bytes;            /* largest arena footprint admitted */
+    double p50_s, p99_s, mean_s, max_s;   /* request latency: submit to results in host memory */
+    double span_s;                        /* first submit to last completion */
+} bed_server_stats;
+
+void bed_server_default_config(bed_server_config* c);
+
+/* Creates a server on the current device. p, t: NULL or parameters / ragged tuning (as for
+ * bed_eigh_ragged_f32). Returns BED_ERR_CUDA if the device or pinned memory cannot be allocated. */
+bed_status bed_server_create(const bed_server_config* cfg, const bed_params* p, const bed_ragged_tuning* t,
+                             bed_server** out);
+
+/* Queues b x n x n FP32 matrices at A_host (host memory that must stay unchanged until the request
+ * completes; pinned memory lets the copy run asynchronously). *request_id identifies it. A request that
+ * alone exceeds the budgets is refused with BED_ERR_TOO_LARGE (it still gets an id to release). */
+bed_status bed_server_submit(bed_server* s, const float* A_host, int32_t b, int32_t n, int64_t* request_id);
+
+/* Waits up to timeout_s seconds (< 0: without limit) for a request; on BED_OK, *V ([b][n][n], columns
+ * are eigenvectors), *W ([b][n], ascending) and *info ([b]) point into the server's pinned result
+ * memory, valid until bed_server_release. Returns the request's status (BED_ERR_TOO_LARGE for a refused
+ * request) or BED_ERR_TIMEOUT. Any pointer argument may be NULL. */
+bed_status bed_server_wait(bed_server* s, int64_t id, double timeout_s, const float** W, const float** V,
+                           const int32_t** info);
+
+/* Returns a completed request's result memory to the server and forgets the id. */
+bed_status bed_server_release(bed_server* s, int64_t id);
+
+bed_status bed_server_get_stats(bed_server* s, bed_server_stats* out);
+bed_status bed_server_reset_stats(bed_server* s);
+
+/* Stops the threads after the queued requests are launched, waits for the device, frees everything. */
+void bed_server_destroy(bed_server* s);
 
 /* Largest supported n (64). */
 int bed_max_n(void);

@@ -19,6 +19,7 @@ BED_ERR_INVALID_ARG = 1
 BED_ERR_UNSUPPORTED_N = 2
 BED_ERR_CUDA = 3
 BED_ERR_TOO_LARGE = 4
+BED_ERR_TIMEOUT = 5
 BED_NOALLOC_MAX_COUNT = 65536
 
 BED_INFO_OK = 0
@@ -55,6 +56,17 @@ class bed_ragged_tuning(C.Structure):
     _fields_ = [("team", C.c_ubyte * 65), ("leaf", C.c_ubyte * 65)]
 
 
+class bed_server_config(C.Structure):
+    _fields_ = [("device_budget_bytes", C.c_size_t), ("host_result_bytes", C.c_size_t), ("streams", C.c_int),
+                ("max_launch_matrices", C.c_int), ("mode", C.c_int)]
+
+
+class bed_server_stats(C.Structure):
+    _fields_ = [("requests", C.c_int64), ("matrices", C.c_int64), ("launches", C.c_int64),
+                ("peak_device_bytes", C.c_int64), ("p50_s", C.c_double), ("p99_s", C.c_double),
+                ("mean_s", C.c_double), ("max_s", C.c_double), ("span_s", C.c_double)]
+
+
 EXPORTED = [
     "bed_default_params",
     "bed_eigh_f32",
@@ -64,6 +76,14 @@ EXPORTED = [
     "bed_eigh_ragged_f32_noalloc",
     "bed_eigh_ragged_workspace_size",
     "bed_ragged_default_tuning",
+    "bed_server_default_config",
+    "bed_server_create",
+    "bed_server_submit",
+    "bed_server_wait",
+    "bed_server_release",
+    "bed_server_get_stats",
+    "bed_server_reset_stats",
+    "bed_server_destroy",
     "bed_max_n",
     "bed_status_string",
     "bed_last_cuda_error",
@@ -97,6 +117,23 @@ def lib() -> C.CDLL:
             L.bed_plan_describe.restype = C.c_int
             L.bed_eigh_backward_f32.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_int, C.c_float, vp]
             L.bed_eigh_backward_f32.restype = C.c_int
+            L.bed_server_default_config.argtypes = [C.POINTER(bed_server_config)]
+            L.bed_server_default_config.restype = None
+            L.bed_server_create.argtypes = [C.POINTER(bed_server_config), C.POINTER(bed_params),
+                                            C.POINTER(bed_ragged_tuning), C.POINTER(vp)]
+            L.bed_server_create.restype = C.c_int
+            L.bed_server_submit.argtypes = [vp, vp, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
+            L.bed_server_submit.restype = C.c_int
+            L.bed_server_wait.argtypes = [vp, C.c_int64, C.c_double, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
+            L.bed_server_wait.restype = C.c_int
+            L.bed_server_release.argtypes = [vp, C.c_int64]
+            L.bed_server_release.restype = C.c_int
+            L.bed_server_get_stats.argtypes = [vp, C.POINTER(bed_server_stats)]
+            L.bed_server_get_stats.restype = C.c_int
+            L.bed_server_reset_stats.argtypes = [vp]
+            L.bed_server_reset_stats.restype = C.c_int
+            L.bed_server_destroy.argtypes = [vp]
+            L.bed_server_destroy.restype = None
             L.bed_ragged_default_tuning.argtypes = [C.POINTER(bed_ragged_tuning)]
             L.bed_ragged_default_tuning.restype = None
             L.bed_eigh_ragged_workspace_size.argtypes = [C.c_int64]
@@ -169,6 +206,51 @@ def bed_eigh_ragged_f32_noalloc(A_ptr: int, offsets_ptr: int, ns_ptr: int, count
     return lib().bed_eigh_ragged_f32_noalloc(A_ptr, offsets_ptr, ns_ptr, count, W_ptr, w_offsets_ptr, V_ptr,
                                              info_ptr, C.byref(params) if params is not None else None,
                                              C.byref(tuning) if tuning is not None else None, counters_ptr, stream)
+
+
+def bed_server_default_config() -> bed_server_config:
+    c = bed_server_config()
+    lib().bed_server_default_config(C.byref(c))
+    return c
+
+
+def bed_server_create(cfg: bed_server_config | None = None, params: bed_params | None = None,
+                      tuning: bed_ragged_tuning | None = None):
+    h = C.c_void_p()
+    st = lib().bed_server_create(C.byref(cfg) if cfg is not None else None,
+                                 C.byref(params) if params is not None else None,
+                                 C.byref(tuning) if tuning is not None else None, C.byref(h))
+    return st, h
+
+
+def bed_server_submit(h, A_ptr: int, b: int, n: int):
+    rid = C.c_int64()
+    st = lib().bed_server_submit(h, A_ptr, b, n, C.byref(rid))
+    return st, rid.value
+
+
+def bed_server_wait(h, rid: int, timeout_s: float = -1.0):
+    W, V, I = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    st = lib().bed_server_wait(h, rid, timeout_s, C.byref(W), C.byref(V), C.byref(I))
+    return st, W.value, V.value, I.value
+
+
+def bed_server_release(h, rid: int) -> int:
+    return lib().bed_server_release(h, rid)
+
+
+def bed_server_get_stats(h) -> bed_server_stats:
+    out = bed_server_stats()
+    _check(lib().bed_server_get_stats(h, C.byref(out)))
+    return out
+
+
+def bed_server_reset_stats(h) -> int:
+    return lib().bed_server_reset_stats(h)
+
+
+def bed_server_destroy(h) -> None:
+    lib().bed_server_destroy(h)
 
 
 def bed_max_n() -> int:

@@ -297,6 +297,7 @@ const char* bed_status_string(bed_status s)
     case BED_ERR_UNSUPPORTED_N: return "BED_ERR_UNSUPPORTED_N";
     case BED_ERR_CUDA: return "BED_ERR_CUDA";
     case BED_ERR_TOO_LARGE: return "BED_ERR_TOO_LARGE";
+    case BED_ERR_TIMEOUT: return "BED_ERR_TIMEOUT";
     }
     return "BED_UNKNOWN_STATUS";
 }
