@@ -41,13 +41,21 @@ struct Smem {
     float A[NMAX * LD];  // matrix; after a1 row k holds reflector k in columns k+2..n-1
     float Q[NMAX * LD];  // eigenvectors of the current blocks (block diagonal)
     float M[NMAX * LD];  // staging of A[b]; merge workspace (rows = sorted poles); a8 workspace
-    float pp[NMAX], vv[NMAX];              // a1: p = tau A22 v and v of the current reflector
     float d[NMAX], e[NMAX], tau[NMAX];     // tridiagonal and reflector scalars
     float lam[NMAX];                       // eigenvalue of each column of Q
     float ds[NMAX], zs[NMAX];              // merge: poles and z in ascending pole order
-    float cd[NMAX], cz[NMAX], cz2[NMAX];   // merge: compacted (non-deflated first) scaled poles, z, z^2
-    float tq[NMAX], zh[NMAX];              // merge: root offsets from their poles, z-hat
-    float rc[NMAX], rs[NMAX];              // merge: Givens deflation rotations (by sorted position)
+    union alignas(16) {  // a1 and the merges never run at the same time
+        struct {
+            float cd[NMAX], cz[NMAX], cz2[NMAX];  // merge: compacted (non-deflated first) scaled poles, z, z^2
+            float tq[NMAX], zh[NMAX];             // merge: root offsets from their poles, z-hat
+            float rc[NMAX], rs[NMAX];             // merge: Givens deflation rotations (by sorted position)
+        };
+        struct {
+            float hp[2][NMAX];  // a1: p = tau A22 v of the last reflector (by step parity)
+            float hu[2][NMAX];  // a1: the last reflector v, 0 before its leading 1
+            float hy[2][NMAX];  // a1: the next column, before the last update
+        };
+    };
     float sgn[NMAX];
     float brho[NB], bnz[NB], btol[NB], bsc[NB];  // per merge of a level: |beta|, |z|, tolerance, scale
     int rank[NMAX];   // column c of the children -> its sorted position
@@ -60,6 +68,10 @@ struct Smem {
     int brot[NB];     // per merge of a level: close-pole rotations present
     float red[32];
     int flag_rot;
+    float unscale;      // 2^e of the input scaling (a0), for the eigenvalues stored in a9
+    float* out_w;       // this matrix's outputs, kept here rather than in registers through a1-a8
+    float* out_v;
+    int32_t* out_info;
     int info;
     unsigned int evals, roots, deflated;
     alignas(8) unsigned long long mbar;
@@ -404,7 +416,12 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
     int ex = 0;
     if (amax > 0.f) frexpf(amax, &ex);
     const float scale = ldexpf(1.f, -ex);
-    const float unscale = ldexpf(1.f, ex);
+    if (tid == 0) {
+        S.unscale = ldexpf(1.f, ex);
+        S.out_w = Wb;
+        S.out_v = Vb;
+        S.out_info = info_b;
+    }
     for (int i = warp; i < n; i += NW)
         for (int j = lane; j <= i; j += 32) {
             const float x = S.M[i * n + j] * scale;
@@ -414,80 +431,192 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
     team_sync<NT>(bar_id);
 
     // ---------------- a1: Householder tridiagonalization ------------------------------------
-    for (int k = 0; k + 2 < n; ++k) {
-        const int r0 = k + 1;
-        const int m = n - r0;
-        // every warp forms reflector k from row k (= column k; the matrix is kept symmetric)
-        const float alpha = S.A[k * LD + r0];
-        float part = 0.f;
-        for (int j = r0 + 1 + lane; j < n; j += 32) {
-            const float x = S.A[k * LD + j];
-            part = fmaf(x, x, part);
-        }
-        const float xn2 = warp_sum(part);
-        float tau = 0.f, beta = alpha, scal = 0.f;
-        if (xn2 > 0.f) {
-            const float nrm = sqrtf(fmaf(alpha, alpha, xn2));
-            beta = (alpha >= 0.f) ? -nrm : nrm;
-            tau = (beta - alpha) / beta;
-            scal = 1.f / (alpha - beta);
-        }
-        // p = tau A22 v with v = [1, scal x]: p_i = tau (A[r0][i] + scal sum_{j>r0} A[j][i] x_j).
-        // G lanes per row i, each over interleaved runs of 8 columns j (the runs of the G lanes of
-        // 32/G consecutive rows fall in distinct banks)
-        {
-            float acc = 0.f;
-            const int i = r0 + pos;
-            if (pos < m) {
+    // Column-owned register tiles, one barrier per reflector. Warp w keeps columns
+    // [w WC, (w + 1) WC) of A in registers: lane (tr, tc) = (lane >> 1, lane & 1) holds rows
+    // [TR tr, TR tr + TR) of columns w WC + TC tc + [0, TC). A is symmetric, so the column sums of a
+    // warp's block are the entries of A v at its columns: p = tau A22 v needs shuffles inside the warp
+    // only. Step k reads three vectors that step k-1 left in shared memory (double-buffered by step
+    // parity): p_{k-1}, v_{k-1} and column k of A before the update of step k-1. From them every warp
+    // forms, redundantly and identically, w_{k-1} = p - (tau/2)(p.v) v, column k of the updated matrix
+    // and reflector k; it applies A22 -= v w^T + w v^T of step k-1 to its tile and forms the column
+    // sums with v_k. A warp whose columns are all finished skips the step.
+    {
+        constexpr int WC = NMAX / NW;             // columns per warp
+        constexpr int TC = WC / 2;                // tile columns per lane
+        constexpr int TR = NMAX / 16;             // tile rows per lane
+        constexpr int NL = (NMAX + 31) / 32;      // entries per lane in the lane layout i = lane + 32 m
+        constexpr int LOG_TC = (TC == 8) ? 3 : (TC == 4 ? 2 : (TC == 2 ? 1 : 0));
+        static_assert(WC * NW == NMAX && TR * 16 == NMAX && (1 << LOG_TC) == TC, "tile shape");
+        const int tr = lane >> 1, tc = lane & 1;
+        const int i0 = tr * TR, j0 = warp * WC + tc * TC;
+        float a[TR][TC];
 #pragma unroll
-                for (int blk = 0; blk < (NMAX + 8 * G - 1) / (8 * G); ++blk)
+        for (int ii = 0; ii < TR; ++ii)
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int j = r0 + 1 + 8 * (sub + G * blk) + u;
-                        if (j < n) acc = fmaf(S.A[j * LD + i], S.A[k * LD + j], acc);
-                    }
+            for (int jj = 0; jj < TC; ++jj) {
+                const int i = i0 + ii, j = j0 + jj;
+                a[ii][jj] = (i < n && j < n) ? S.A[i * LD + j] : 0.f;
             }
-            acc = gsum<G>(acc);
-            if (pos < m && sub == 0) {
-                S.pp[i] = tau * fmaf(scal, acc, S.A[r0 * LD + i]);
-                S.vv[i] = (i == r0) ? 1.f : S.A[k * LD + i] * scal;
-            }
+        // step 0 reads buffer 1: p = v = 0 and column 0 of A
+        for (int i = tid; i < NMAX; i += NT) {
+            S.hp[0][i] = 0.f;
+            S.hu[0][i] = 0.f;
+            S.hy[0][i] = 0.f;
+            S.hp[1][i] = 0.f;
+            S.hu[1][i] = 0.f;
+            S.hy[1][i] = (i < n) ? S.A[i * LD] : 0.f;
         }
-        if (tid == 0) {
-            S.d[k] = S.A[k * LD + k];
-            S.e[k] = beta;
-            S.tau[k] = tau;
-        }
-        team_sync<NT>(bar_id);
-        // w = p - (tau/2)(p.v) v (every warp forms p.v); A22 -= v w^T + w v^T; row k keeps v
-        {
-            float pvp = 0.f;
-            for (int i = r0 + lane; i < n; i += 32) pvp = fmaf(S.pp[i], S.vv[i], pvp);
-            const float c = 0.5f * tau * warp_sum(pvp);
-            if (col < m) {
-                const int j = r0 + col;
-                const float vj = S.vv[j];
-                const float wj = fmaf(-c, vj, S.pp[j]);
-                for (int i = r0 + grp; i < n; i += G) {
-                    const float vi = S.vv[i];
-                    const float wi = fmaf(-c, vi, S.pp[i]);
-                    S.A[i * LD + j] -= fmaf(vi, wj, wi * vj);
+        team_sync<NT>(bar_id);  // every tile is loaded before row k of S.A takes reflector k
+        const int wlast = (n - 1) / WC;  // owns column n - 1: active in every step; stores reflectors
+        float tau_prev = 0.f;
+        for (int k = 0; k + 2 < n; ++k) {
+            const float* Pr = S.hp[(k + 1) & 1];
+            const float* Ur = S.hu[(k + 1) & 1];
+            const float* Yr = S.hy[(k + 1) & 1];
+            float tau = 0.f;
+            if (warp * WC + WC > k + 1 && warp <= wlast) {
+                // c = (tau/2) p.v of step k - 1, in the lane layout
+                float dot = 0.f;
+#pragma unroll
+                for (int m = 0; m < NL; ++m) {
+                    const int i = lane + 32 * m;
+                    if (i < NMAX) dot = fmaf(Pr[i], Ur[i], dot);
                 }
-                if (grp == 0 && j > r0) S.A[k * LD + j] = vj;
+                const float c = 0.5f * tau_prev * warp_sum(dot);
+                const float uk = Ur[k];
+                const float wk = fmaf(-c, uk, Pr[k]);
+                // x = column k of the updated matrix, rows k + 1 ..
+                float part = 0.f;
+                float xl[NL];
+#pragma unroll
+                for (int m = 0; m < NL; ++m) {
+                    const int i = lane + 32 * m;
+                    xl[m] = 0.f;
+                    if (i < NMAX) {
+                        const float u = Ur[i];
+                        xl[m] = fmaf(-fmaf(-c, u, Pr[i]), uk, fmaf(-u, wk, Yr[i]));
+                    }
+                    if (i > k + 1 && i < n) part = fmaf(xl[m], xl[m], part);
+                }
+                const float xn2 = warp_sum(part);
+                const float u1 = Ur[k + 1];
+                const float alpha = fmaf(-fmaf(-c, u1, Pr[k + 1]), uk, fmaf(-u1, wk, Yr[k + 1]));
+                float beta = alpha, scal = 0.f;
+                if (xn2 > 0.f) {
+                    const float nrm = sqrtf(fmaf(alpha, alpha, xn2));
+                    beta = (alpha >= 0.f) ? -nrm : nrm;
+                    tau = (beta - alpha) / beta;
+                    scal = 1.f / (alpha - beta);
+                }
+                // update of step k - 1 on the tile (rows and columns >= k), then the column sums of
+                // the updated tile with v_k
+                float ur[TR], wr[TR], vr[TR];
+#pragma unroll
+                for (int ii = 0; ii < TR; ++ii) {
+                    const int i = i0 + ii;
+                    const float u = Ur[i], p = Pr[i];
+                    ur[ii] = u;
+                    wr[ii] = (i >= k) ? fmaf(-c, u, p) : 0.f;
+                    const float x = fmaf(-fmaf(-c, u, p), uk, fmaf(-u, wk, Yr[i]));
+                    vr[ii] = (i > k + 1) ? x * scal : ((i == k + 1) ? 1.f : 0.f);
+                }
+                float s[TC];
+#pragma unroll
+                for (int jj = 0; jj < TC; ++jj) {
+                    const int j = j0 + jj;
+                    const float u = Ur[j];
+                    const float w = (j >= k) ? fmaf(-c, u, Pr[j]) : 0.f;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int ii = 0; ii < TR; ++ii) {
+                        a[ii][jj] = fmaf(-ur[ii], w, fmaf(-wr[ii], u, a[ii][jj]));
+                        acc = fmaf(a[ii][jj], vr[ii], acc);
+                    }
+                    s[jj] = acc;
+                }
+                // sum over the 16 row lanes: halving exchanges leave lane bits 1.. LOG_TC holding one
+                // column each, plain butterflies finish the sum
+                int cb = 0;
+#pragma unroll
+                for (int l = 0; l < LOG_TC; ++l) {
+                    const int h = TC >> (l + 1);
+                    const int o = 2 << l;
+                    const bool up = (lane & o) != 0;
+#pragma unroll
+                    for (int t = 0; t < h; ++t) {
+                        const float send = up ? s[t] : s[t + h];
+                        const float keep = up ? s[t + h] : s[t];
+                        s[t] = keep + __shfl_xor_sync(kFull, send, o);
+                    }
+                    if (up) cb += h;
+                }
+#pragma unroll
+                for (int o = 2 << LOG_TC; o < 32; o <<= 1) s[0] += __shfl_xor_sync(kFull, s[0], o);
+                float* Pw = S.hp[k & 1];
+                if ((lane >> (1 + LOG_TC)) == 0) Pw[j0 + cb] = tau * s[0];
+                // column k + 1 of the updated matrix, for step k + 1
+                if (warp == (k + 1) / WC && tc == ((k + 1) % WC) / TC) {
+                    const int kj = (k + 1) % TC;
+                    float* Yw = S.hy[k & 1];
+#pragma unroll
+                    for (int ii = 0; ii < TR; ++ii) {
+                        float x = 0.f;
+#pragma unroll
+                        for (int jj = 0; jj < TC; ++jj) x = (jj == kj) ? a[ii][jj] : x;
+                        Yw[i0 + ii] = x;
+                    }
+                }
+                if (warp == wlast) {
+                    float* Uw = S.hu[k & 1];
+#pragma unroll
+                    for (int m = 0; m < NL; ++m) {
+                        const int i = lane + 32 * m;
+                        if (i < NMAX) {
+                            const float v = (i > k + 1 && i < n) ? xl[m] * scal : ((i == k + 1) ? 1.f : 0.f);
+                            Uw[i] = v;
+                            if (i > k + 1 && i < n) S.A[k * LD + i] = v;
+                        }
+                    }
+                    if (lane == 0) {
+                        S.d[k] = fmaf(-2.f * uk, wk, Yr[k]);
+                        S.e[k] = beta;
+                        S.tau[k] = tau;
+                    }
+                }
             }
+            tau_prev = tau;
+            team_sync<NT>(bar_id);
+        }
+        // the trailing 2 x 2 block after the last update (the whole matrix when n <= 2)
+        const int kf = n - 2;
+        if (n >= 2 && warp * WC + WC > kf && warp <= wlast) {
+            const float* Pr = S.hp[(kf + 1) & 1];
+            const float* Ur = S.hu[(kf + 1) & 1];
+            float dot = 0.f;
+#pragma unroll
+            for (int m = 0; m < NL; ++m) {
+                const int i = lane + 32 * m;
+                if (i < NMAX) dot = fmaf(Pr[i], Ur[i], dot);
+            }
+            const float c = 0.5f * tau_prev * warp_sum(dot);
+#pragma unroll
+            for (int ii = 0; ii < TR; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < TC; ++jj) {
+                    const int i = i0 + ii, j = j0 + jj;
+                    if (i >= kf && j >= kf && i < n && j < n && j <= i) {
+                        const float ui = Ur[i], uj = Ur[j];
+                        const float wi = fmaf(-c, ui, Pr[i]), wj = fmaf(-c, uj, Pr[j]);
+                        const float x = fmaf(-ui, wj, fmaf(-wi, uj, a[ii][jj]));
+                        if (i == j) S.d[i] = x;
+                        else S.e[kf] = x;
+                    }
+                }
+        } else if (n == 1 && tid == 0) {
+            S.d[0] = a[0][0];
         }
         team_sync<NT>(bar_id);
     }
-    if (tid == 0) {
-        if (n >= 2) {
-            S.d[n - 2] = S.A[(n - 2) * LD + n - 2];
-            S.d[n - 1] = S.A[(n - 1) * LD + n - 1];
-            S.e[n - 2] = S.A[(n - 1) * LD + n - 2];
-        } else {
-            S.d[0] = S.A[0];
-        }
-    }
-    team_sync<NT>(bar_id);
 
     // ---------------- a2: tear (Eq. (3)) ----------------------------------------------------
     if (tid < n) {
@@ -936,14 +1065,14 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         }
         if (pos < n && sub == 0) {
             S.sgn[pos] = (S.Q[im * LD + src] < 0.f) ? -1.f : 1.f;
-            Wb[pos] = S.lam[src] * unscale;
+            S.out_w[pos] = S.lam[src] * S.unscale;
         }
     }
     team_sync<NT>(bar_id);
     for (int i = warp; i < n; i += NW)
-        for (int j = lane; j < n; j += 32) Vb[i * n + j] = S.sgn[j] * S.Q[i * LD + S.outc[j]];
+        for (int j = lane; j < n; j += 32) S.out_v[i * n + j] = S.sgn[j] * S.Q[i * LD + S.outc[j]];
     if (tid == 0) {
-        if (info_b) *info_b = S.info;
+        if (S.out_info) *S.out_info = S.info;
         if (counters) {
             atomicAdd(&counters->matrices, 1ull);
             atomicAdd(&counters->roots, static_cast<unsigned long long>(S.roots));
@@ -958,8 +1087,21 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
 // ---------------------------------------------------------------------------------------------
 // Uniform-size kernel: one team = one thread block, matrices b = blockIdx.x, blockIdx.x + gridDim.x, ...
 // ---------------------------------------------------------------------------------------------
+// Blocks per SM the launch bounds promise: as many as 64 registers a thread allows, but no more than
+// the shared memory lets reside (228 KB per SM, 1 KB of it reserved per block), so that a block whose
+// residency is set by shared memory gets the registers that it can use (the 64 x 64 team of 128
+// threads: 4 blocks, 128 registers).
 template <int NMAX, int G>
-__global__ void __launch_bounds__(NMAX * G, 65536 / (NMAX * G * 64))
+constexpr int eigh_min_blocks()
+{
+    constexpr int by_regs = 65536 / (NMAX * G * 64);
+    constexpr int by_smem = static_cast<int>((228 * 1024) / (sizeof(Smem<NMAX, G>) + 1024));
+    constexpr int m = by_regs < by_smem ? by_regs : by_smem;
+    return m < 1 ? 1 : m;
+}
+
+template <int NMAX, int G>
+__global__ void __launch_bounds__(NMAX * G, eigh_min_blocks<NMAX, G>())
     eigh_kernel(const float* __restrict__ A, float* __restrict__ W, float* __restrict__ V,
                 int32_t* __restrict__ info, int64_t batch, const __grid_constant__ Plan plan,
                 const KParams kp, bed_counters* __restrict__ counters, int bulk)
