@@ -38,9 +38,9 @@ template <int NMAX, int G>
 struct Smem {
     static constexpr int LD = NMAX + 1;  // odd stride: column walks hit distinct banks
     static constexpr int NB = NMAX / 2;  // merges per level, at most
-    float A[NMAX * LD];  // matrix; after a1 row k holds reflector k in columns k+2..n-1
+    alignas(16) float A[NMAX * LD];  // matrix; after a1 the reflectors, transposed (yt_index)
     float Q[NMAX * LD];  // eigenvectors of the current blocks (block diagonal)
-    float M[NMAX * LD];  // staging of A[b]; merge workspace (rows = sorted poles); a8 workspace
+    alignas(16) float M[NMAX * LD];  // staging of A[b]; merge workspace (rows = sorted poles); a8 workspace
     float d[NMAX], e[NMAX], tau[NMAX];     // tridiagonal and reflector scalars
     float lam[NMAX];                       // eigenvalue of each column of Q
     float ds[NMAX], zs[NMAX];              // merge: poles and z in ascending pole order
@@ -133,6 +133,16 @@ __device__ __forceinline__ float rcp_approx(float x)
 
 // Sort key with a total order: NaN sorts last, ties broken by index by the callers.
 __device__ __forceinline__ float sort_key(float x) { return isnan(x) ? INFINITY : x; }
+
+// Reflectors of a1, stored transposed over the storage of S.A once a1 has read the matrix: entry i of
+// v_k at Yt[i * NMAX + k], with the 4-float chunks of each row permuted by an XOR of the row index so
+// that 16-byte reads of rows i, i + 1, i + 2, i + 3 at the same column fall in distinct banks.
+template <int NMAX>
+__device__ __forceinline__ int yt_index(int i, int k)
+{
+    constexpr int SW = (NMAX / 4 < 8 ? NMAX / 4 : 8) - 1;
+    return i * NMAX + ((((k >> 2) ^ (i & SW)) << 2) | (k & 3));
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -574,7 +584,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                         if (i < NMAX) {
                             const float v = (i > k + 1 && i < n) ? xl[m] * scal : ((i == k + 1) ? 1.f : 0.f);
                             Uw[i] = v;
-                            if (i > k + 1 && i < n) S.A[k * LD + i] = v;
+                            S.A[yt_index<NMAX>(i, k)] = v;
                         }
                     }
                     if (lane == 0) {
@@ -586,6 +596,11 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             }
             tau_prev = tau;
             team_sync<NT>(bar_id);
+        }
+        // reflector columns n - 2 .. of the last back-transform block are zero
+        for (int idx = tid; idx < NMAX * kBT; idx += NT) {
+            const int i = idx / kBT, kk = n - 2 + idx % kBT;
+            if (n >= 3 && kk < NMAX) S.A[yt_index<NMAX>(i, kk)] = 0.f;
         }
         // the trailing 2 x 2 block after the last update (the whole matrix when n <= 2)
         const int kf = n - 2;
@@ -915,17 +930,20 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
 
     // ---------------- a8: back-transform V = H_0 ... H_{n-3} Q_T ----------------------------
     // Blocks of kBT reflectors: H_{k0} ... H_{k0+b-1} = I - Y T Y^T with T upper triangular
-    // (forward accumulation); Y[i][r] = v_{k0+r}[i] is 0 above row k0+r+1, 1 on it and row k0+r
-    // of A below it. Blocks are applied last to first: Q <- Q - Y (T (Y^T Q)).
+    // (forward accumulation); column r of Y is v_{k0+r}, zero above its unit entry. Blocks are applied
+    // last to first, Q <- Q - Y (T (Y^T Q)), with column pos of Q held in registers by its G lanes
+    // (rows sub + G t): Y^T Q is a sum over those lanes, so no barrier separates the blocks.
     if (n >= 3) {
         const int nr = n - 2;
         const int ngr = (nr + kBT - 1) / kBT;
-        float* Tm = S.M;                    // ngr blocks of kBT x kBT: T above the diagonal, Gram below
-        float* W1 = S.M + ngr * kBT * kBT;  // kBT x NMAX
+        const float* Yt = S.A;
+        float* Tm = S.M;  // ngr blocks of kBT x kBT, row-major; zero below the diagonal
         for (int g = warp; g < ngr; g += NW) {
             const int k0 = g * kBT;
             const int bsz = min(kBT, nr - k0);
             float* T = Tm + g * kBT * kBT;
+            for (int e = lane; e < kBT * kBT; e += 32) T[e] = 0.f;
+            __syncwarp();
             // Gram entries Y[:, r]^T Y[:, j] for r < j, one pair per lane, stored at T[j][r]
             int p = lane, r = 0;
             while (r < kBT - 1 && p >= kBT - 1 - r) {
@@ -935,9 +953,10 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             const int j = r + 1 + p;
             if (r < kBT - 1 && j < bsz) {
                 const int kr = k0 + r, kj = k0 + j;
-                float s = S.A[kr * LD + kj + 1];  // Y[kj+1][r] times Y[kj+1][j] = 1
-                for (int i = kj + 2; i < n; ++i) s = fmaf(S.A[kr * LD + i], S.A[kj * LD + i], s);
-                T[j * kBT + r] = s;
+                float sg = 0.f;
+                for (int i = kj + 1; i < n; ++i)
+                    sg = fmaf(Yt[yt_index<NMAX>(i, kr)], Yt[yt_index<NMAX>(i, kj)], sg);
+                T[j * kBT + r] = sg;
             }
             __syncwarp();
             // T[jj][jj] = tau_jj; T[0:jj, jj] = T[0:jj, 0:jj] w with w_s = -tau_jj Gram[s][jj]
@@ -954,76 +973,81 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 if (lane == jj) T[jj * kBT + jj] = tj;
                 __syncwarp();
             }
+            for (int e = lane; e < kBT * kBT; e += 32)
+                if (e % kBT < e / kBT) T[e] = 0.f;
         }
         team_sync<NT>(bar_id);
+        static_assert(kBT == 8, "two 16-byte reads per row of a block");
+        constexpr int RPT = NMAX / G;
+        float q[RPT];
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) {
+            const int i = sub + G * t;
+            q[t] = (pos < n && i < n) ? S.Q[i * LD + pos] : 0.f;
+        }
         for (int g = ngr - 1; g >= 0; --g) {
             const int k0 = g * kBT;
-            const int bsz = min(kBT, nr - k0);
             const float* T = Tm + g * kBT * kBT;
-            // W1 = Y^T Q (bsz x n): this thread's rows r = grp + G*rr of W1, one pass over Q's column;
-            // rows i <= k0 + kBT hold the unit and zero entries of Y, the rows below are plain
-            constexpr int RB = (kBT + G - 1) / G;
-            if (col < n) {
-                float acc[RB];
+            // W1 = Y^T q over this lane's rows; rows up to k0 are zero in every column of Y
+            float w1[kBT];
 #pragma unroll
-                for (int rr = 0; rr < RB; ++rr) acc[rr] = 0.f;
-                const int iedge = min(k0 + kBT, n - 1);
-                for (int i = k0 + 1; i <= iedge; ++i) {
-                    const float qv = S.Q[i * LD + col];
+            for (int r = 0; r < kBT; ++r) w1[r] = 0.f;
 #pragma unroll
-                    for (int rr = 0; rr < RB; ++rr) {
-                        const int kr = k0 + grp + G * rr;
-                        const float y = (i > kr + 1) ? S.A[kr * LD + i] : ((i == kr + 1) ? 1.f : 0.f);
-                        acc[rr] = fmaf(y, qv, acc[rr]);
-                    }
-                }
-                for (int i = iedge + 1; i < n; ++i) {
-                    const float qv = S.Q[i * LD + col];
-#pragma unroll
-                    for (int rr = 0; rr < RB; ++rr)
-                        acc[rr] = fmaf(S.A[(k0 + grp + G * rr) * LD + i], qv, acc[rr]);
-                }
-#pragma unroll
-                for (int rr = 0; rr < RB; ++rr) {
-                    const int r = grp + G * rr;
-                    if (r < bsz) W1[r * NMAX + col] = acc[rr];
-                }
+            for (int t = 0; t < RPT; ++t) {
+                if (G * t + G - 1 <= k0) continue;
+                const int i = sub + G * t;
+                const float4 ya = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0));
+                const float4 yb = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0 + 4));
+                w1[0] = fmaf(ya.x, q[t], w1[0]);
+                w1[1] = fmaf(ya.y, q[t], w1[1]);
+                w1[2] = fmaf(ya.z, q[t], w1[2]);
+                w1[3] = fmaf(ya.w, q[t], w1[3]);
+                w1[4] = fmaf(yb.x, q[t], w1[4]);
+                w1[5] = fmaf(yb.y, q[t], w1[5]);
+                w1[6] = fmaf(yb.z, q[t], w1[6]);
+                w1[7] = fmaf(yb.w, q[t], w1[7]);
             }
-            team_sync<NT>(bar_id);
-            // Q -= Y (T W1)
-            if (col < n) {
-                float w2[kBT];
 #pragma unroll
-                for (int r = 0; r < kBT; ++r) {
-                    float s = 0.f;
-                    if (r < bsz)
-                        for (int s2 = r; s2 < bsz; ++s2) s = fmaf(T[r * kBT + s2], W1[s2 * NMAX + col], s);
-                    w2[r] = s;
-                }
-                // rows k0+r of A with r >= bsz are not reflectors (possibly never written): skip them
-                int i = k0 + 1 + grp;
-                for (; i <= k0 + kBT && i < n; i += G) {
-                    float acc = S.Q[i * LD + col];
+            for (int r = 0; r < kBT; ++r) w1[r] = gsum<G>(w1[r]);
+            // W2 = T W1
+            float w2[kBT];
 #pragma unroll
-                    for (int r = 0; r < kBT; ++r) {
-                        const int kr = k0 + r;
-                        if (r < bsz) {
-                            const float y = (i > kr + 1) ? S.A[kr * LD + i] : ((i == kr + 1) ? 1.f : 0.f);
-                            acc = fmaf(-y, w2[r], acc);
-                        }
-                    }
-                    S.Q[i * LD + col] = acc;
-                }
-                for (; i < n; i += G) {
-                    float acc = S.Q[i * LD + col];
-#pragma unroll
-                    for (int r = 0; r < kBT; ++r)
-                        if (r < bsz) acc = fmaf(-S.A[(k0 + r) * LD + i], w2[r], acc);
-                    S.Q[i * LD + col] = acc;
-                }
+            for (int r = 0; r < kBT; ++r) {
+                const float4 ta = *reinterpret_cast<const float4*>(T + r * kBT);
+                const float4 tb = *reinterpret_cast<const float4*>(T + r * kBT + 4);
+                float sacc = ta.x * w1[0];
+                sacc = fmaf(ta.y, w1[1], sacc);
+                sacc = fmaf(ta.z, w1[2], sacc);
+                sacc = fmaf(ta.w, w1[3], sacc);
+                sacc = fmaf(tb.x, w1[4], sacc);
+                sacc = fmaf(tb.y, w1[5], sacc);
+                sacc = fmaf(tb.z, w1[6], sacc);
+                w2[r] = fmaf(tb.w, w1[7], sacc);
             }
-            team_sync<NT>(bar_id);
+            // q -= Y W2
+#pragma unroll
+            for (int t = 0; t < RPT; ++t) {
+                if (G * t + G - 1 <= k0) continue;
+                const int i = sub + G * t;
+                const float4 ya = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0));
+                const float4 yb = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0 + 4));
+                float v = q[t];
+                v = fmaf(-ya.x, w2[0], v);
+                v = fmaf(-ya.y, w2[1], v);
+                v = fmaf(-ya.z, w2[2], v);
+                v = fmaf(-ya.w, w2[3], v);
+                v = fmaf(-yb.x, w2[4], v);
+                v = fmaf(-yb.y, w2[5], v);
+                v = fmaf(-yb.z, w2[6], v);
+                q[t] = fmaf(-yb.w, w2[7], v);
+            }
         }
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) {
+            const int i = sub + G * t;
+            if (pos < n && i < n) S.Q[i * LD + pos] = q[t];
+        }
+        team_sync<NT>(bar_id);
     }
 
     // ---------------- a9: ascending order, signs, store ------------------------------------
