@@ -3,7 +3,8 @@
 
 Workload (one step): the uniform-size covariance batches -- 512 FP32 matrices A = X X^T/m + 1e-3 I
 (X an n x 2n seeded N(0,1) matrix) at each n in {16, 32, 48, 64}, i.e. 2048 eigendecompositions per
-step, one launch per n on one stream. Metric: matrices/s at the stated error (the GPU tests hold every
+step, one launch per n, each on its own stream (forked from and joined to the timing stream) so that the
+four launches run side by side. Metric: matrices/s at the stated error (the GPU tests hold every
 config to the oracle within tolerance).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -11,8 +12,8 @@ config to the oracle within tolerance).
 Timing: W untimed steps, then exactly K steps, each bracketed by CUDA events on the launching stream;
 the L2 is flushed (a 512 MB write) before every step, outside the events. Barrier + synchronize on both
 sides of the timed region, max over ranks. The end-to-end number runs the same workload through the
-public API from pinned host memory (host->device copy, kernels, device->host copy of W, V and info)
-with a wall clock. ``--impl reference`` times the FP64 oracle (a deliberately plain CPU program) on the
+public API from pinned host memory (batched_eigh_many: per n a stream with the host->device copy, the
+kernel and the device->host copies of W, V and info) with a wall clock. ``--impl reference`` times the FP64 oracle (a deliberately plain CPU program) on the
 host cores instead.
 """
 from __future__ import annotations
@@ -287,12 +288,30 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    # one stream per n, forked from and joined to the timing stream: the four launches run side by side
+    side = {n: torch.cuda.Stream(dev) for n in SIZES}
+    order = sorted(SIZES, reverse=True)  # the longest launch first
 
-    def launch(n):
+    def launch(n, s=None):
         st = B.bed_eigh_f32(Ad[n].data_ptr(), Wd[n].data_ptr(), Vd[n].data_ptr(), Id[n].data_ptr(), BATCH, n,
-                            None, sp)
+                            None, (s or stream).cuda_stream)
         if st != B.BED_OK:
             raise B.BedError(B.bed_status_string(st) + " " + B.bed_last_cuda_error())
+
+    def step(evs=None):
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for n in order:
+            s = side[n]
+            s.wait_event(fork)
+            if evs is not None:
+                evs[n][0].record(s)
+            launch(n, s)
+            if evs is not None:
+                evs[n][1].record(s)
+            join = torch.cuda.Event()
+            join.record(s)
+            stream.wait_event(join)
 
     # secular-iteration counts for the FLOP model (one counted pass, outside the timing)
     kbar = {}
@@ -310,12 +329,13 @@ def run_ours(args, rank, world, local):
 
     for i in range(args.warmup):
         flush.fill_(float(i))
-        for n in SIZES:
-            launch(n)
+        step()
     torch.cuda.synchronize(dev)
 
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(SIZES) + 1)] for _ in range(K)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    evn = [{n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in SIZES}
+           for _ in range(K)]
     sampler = ClockSampler(local).start()
     time.sleep(0.3)
     barrier(world)
@@ -324,9 +344,8 @@ def run_ours(args, rank, world, local):
     for s in range(K):
         flush.fill_(float(s))  # > L2: every step starts cold
         ev[s][0].record(stream)
-        for j, n in enumerate(SIZES):
-            launch(n)
-            ev[s][j + 1].record(stream)
+        step(evn[s])
+        ev[s][1].record(stream)
     torch.cuda.synchronize(dev)
     t_end = time.time()
     barrier(world)
@@ -334,7 +353,8 @@ def run_ours(args, rank, world, local):
     clocks = ClockSampler.summarize(rows, t_start, t_end)
 
     step_ms = [ev[s][0].elapsed_time(ev[s][-1]) for s in range(K)]
-    per_n_ms = {n: [ev[s][j].elapsed_time(ev[s][j + 1]) for s in range(K)] for j, n in enumerate(SIZES)}
+    # each launch's own duration, on its stream, while the others run beside it
+    per_n_ms = {n: [evn[s][n][0].elapsed_time(evn[s][n][1]) for s in range(K)] for n in SIZES}
     total_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = total_ms / K
     per_step_units = BATCH * len(SIZES)
@@ -344,8 +364,11 @@ def run_ours(args, rank, world, local):
     peaks = measured_peaks()
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz_max * 1e6 / 1e12  # TFLOP/s
-    dom = max(SIZES, key=lambda n: statistics.mean(per_n_ms[n]))
+    # the dominant kernel: the launch with the most algorithmic work (n = 64), timed on its own stream
+    # while the other three run beside it
+    dom = max(SIZES, key=lambda n: flops_per_matrix(n, kbar[n]))
     t_dom = statistics.mean(per_n_ms[dom]) / 1e3
+    step_flops = sum(flops_per_matrix(n, kbar[n]) * BATCH for n in SIZES)
     achieved = flops_per_matrix(dom, kbar[dom]) * BATCH / t_dom / 1e12
     traffic = read_traffic() if dom == 64 else None
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -470,16 +493,14 @@ def run_ours(args, rank, world, local):
                                            "fifo_per_request_launches": {k: base_s.get(k) for k in keep}}
 
     # end to end through the public API with host buffers
-    host = {n: torch.from_numpy(inputs[n]).pin_memory() for n in SIZES}
+    host = [torch.from_numpy(inputs[n]).pin_memory() for n in SIZES]
     for _ in range(max(1, min(args.warmup, 3))):
-        for n in SIZES:
-            B.batched_eigh(host[n])
+        B.batched_eigh_many(host)
     barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(K):
-        for n in SIZES:
-            B.batched_eigh(host[n])
+        B.batched_eigh_many(host)
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     barrier(world)
@@ -488,7 +509,8 @@ def run_ours(args, rank, world, local):
 
     best_uniform = max(value, uniform_via_ragged)
     launch = ("one ragged persistent launch (plus its one-block ordering pass) per step, CUDA-graph replay"
-              if uniform_via_ragged > value else "one launch per n on one stream")
+              if uniform_via_ragged > value else
+              "one launch per n, each on its own stream forked from and joined to the timing stream")
     line = {
         "metric": METRIC, "value": best_uniform, "unit": "matrices/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -504,7 +526,9 @@ def run_ours(args, rank, world, local):
         "kbar": {str(n): kbar[n] for n in SIZES},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic,
-                     "kernel": f"eigh_kernel n={dom} batch={BATCH}",
+                     "kernel": f"eigh_kernel n={dom} batch={BATCH} (duration on its stream, concurrent with "
+                               f"the other sizes)",
+                     "step_achieved": step_flops / (ms_per_step / 1e3) / 1e12,
                      "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_mhz_max:.0f} MHz",
                      "hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm / hbm_peak,
                              "frac_of_8tbs": hbm / 8000.0}},

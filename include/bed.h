@@ -66,8 +66,9 @@ typedef struct {
     float section_rel_eps;   /* Eq. (17): sectioning stops when U - L < eps * (initial bracket), (0,1) (default 2^-2) */
     float stop_c;            /* Halley stops when |f| <= stop_c * u * (1 + rho sum|z^2/(d - lambda)|), u = 2^-24 (default 8) */
     float deflation_tol_scale; /* deflation tolerance = scale * u * max(max|d|, rho |z|^2) (default 8) */
-    int threads_per_matrix;  /* 0 = automatic; otherwise 2*nmax or 4*nmax threads, nmax in {16, 32, 64} the
-                                smallest that holds n */
+    int threads_per_matrix;  /* 0 = automatic (4*nmax, nmax the smallest of {16, 32, 48, 64} that holds n);
+                                otherwise 2*nmax or 4*nmax for an nmax of that set with nmax >= n, the
+                                smallest such nmax when two match (64 = 4*16 or 2*32; 128 = 4*32 or 2*64) */
     int retire_by_vote;      /* 1 (default): a warp stops iterating secular roots as soon as all of its lanes
                                 have converged (the recast of the paper's progressive batch shrinkage,
                                 Eq. (22)); 0: every warp runs to the iteration caps with converged lanes
@@ -199,8 +200,10 @@ bed_status bed_eigh_backward_f32(const float* W, const float* V, const float* gW
  * `device_budget_bytes` and their results fit `host_result_bytes` of pinned host memory; everything
  * admitted since the previous launch is solved by one ragged launch (bed_eigh_ragged_f32) on a free
  * one of `streams` streams, so requests that arrive while others run are admitted as memory and
- * streams free up and their work overlaps on the device. mode 1 instead runs one uniform-size launch
- * per request, first come first served, on one stream (the plain per-request baseline).
+ * streams free up and their work overlaps on the device. A launch that carries a single request uses the
+ * uniform kernel with the ragged kernel's team shape and leaf size for its n, so a request's results are
+ * the same whether or not it shared a launch. mode 1 instead runs one uniform-size launch (default
+ * parameters) per request, first come first served, on one stream (the plain per-request baseline).
  * The server allocates its device and pinned host memory once, in bed_server_create, and owns two
  * threads; every entry point below is thread-safe.
  */

@@ -307,6 +307,16 @@ def batched_eigh(A: torch.Tensor, params: bed_params | None = None, check: bool 
     memory, solved, and the results are copied back (the end-to-end path). ``check=True`` synchronizes
     and raises if any matrix reports a non-zero info.
     """
+    out = _eigh_enqueue(A, params, counters)
+    if out[3]:
+        torch.cuda.current_stream(out[0].device if out[0].is_cuda else None).synchronize()
+    return _eigh_finish(out, check, return_info)
+
+
+def _eigh_enqueue(A: torch.Tensor, params, counters):
+    """Enqueues the solve of one uniform batch on the current stream; for a CPU tensor also the copies to
+    and from the device (results land in pinned host tensors once the stream reaches them).
+    Returns (W, V, info, host, lead, n)."""
     if A.dtype != torch.float32:
         raise TypeError("batched_eigh expects float32 matrices")
     if A.dim() < 2 or A.shape[-1] != A.shape[-2]:
@@ -340,8 +350,12 @@ def batched_eigh(A: torch.Tensor, params: bed_params | None = None, check: bool 
         Wh.copy_(W, non_blocking=True)
         Vh.copy_(V, non_blocking=True)
         Ih.copy_(info, non_blocking=True)
-        torch.cuda.current_stream(dev).synchronize()
         W, V, info = Wh, Vh, Ih
+    return W, V, info, host, lead, n
+
+
+def _eigh_finish(out, check: bool, return_info: bool):
+    W, V, info, host, lead, n = out
     if check:
         bad = int((info != 0).sum().item())
         if bad:
@@ -428,6 +442,58 @@ class RaggedBatch:
             o, w = self.offsets_list[k], self.woffsets_list[k]
             out.append((self.W[w: w + n], self.V[o: o + n * n].view(n, n)))
         return out
+
+
+_side_streams: dict = {}
+
+
+def _streams(dev: torch.device, k: int):
+    lst = _side_streams.setdefault(dev.index, [])
+    while len(lst) < k:
+        lst.append(torch.cuda.Stream(dev))
+    return lst[:k]
+
+
+def batched_eigh_many(mats, params: bed_params | None = None, check: bool = False,
+                      return_info: bool = False):
+    """Eigendecompositions of several uniform batches: a list of FP32 tensors ``[..., n_i, n_i]``, all on
+    the CPU or all on one CUDA device.
+
+    Each batch gets one launch on its own stream, forked from the current stream and joined back to it,
+    so that batches of different n run side by side on the GPU instead of one after another. For CPU
+    tensors each stream also carries its batch's copy to the device and the copies of its results back,
+    overlapping the other batches' kernels; the call returns once all results are in host memory.
+    Returns a list of ``(W, V)`` (``(W, V, info)`` with ``return_info``), in the order of ``mats``."""
+    mats = list(mats)
+    if not mats:
+        return []
+    if not torch.cuda.is_available():
+        raise BedError("batched_eigh_many needs a CUDA device; there is no CPU path")
+    host = not mats[0].is_cuda
+    if any((not M.is_cuda) != host for M in mats):
+        raise ValueError("batched_eigh_many expects all batches on the CPU or all on one CUDA device")
+    dev = torch.device("cuda", torch.cuda.current_device()) if host else mats[0].device
+    if not host and any(M.device != dev for M in mats):
+        raise ValueError("batched_eigh_many expects all batches on one CUDA device")
+    cur = torch.cuda.current_stream(dev)
+    fork = torch.cuda.Event()
+    fork.record(cur)
+    # largest n first: its launch is the longest and should start first
+    order = sorted(range(len(mats)), key=lambda i: -mats[i].shape[-1])
+    outs = [None] * len(mats)
+    for i, s in zip(order, _streams(dev, len(mats))):
+        s.wait_event(fork)
+        with torch.cuda.stream(s):
+            outs[i] = _eigh_enqueue(mats[i], params, None)
+        join = torch.cuda.Event()
+        join.record(s)
+        cur.wait_event(join)
+        if not host:
+            for t in outs[i][:3]:
+                t.record_stream(cur)
+    if host:
+        cur.synchronize()
+    return [_eigh_finish(o, check, return_info) for o in outs]
 
 
 def batched_eigh_ragged(mats, params: bed_params | None = None, tuning: bed_ragged_tuning | None = None,

@@ -90,6 +90,8 @@ cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int
     BED_CASE(16, 4)
     BED_CASE(32, 2)
     BED_CASE(32, 4)
+    BED_CASE(48, 2)
+    BED_CASE(48, 4)
     BED_CASE(64, 2)
     BED_CASE(64, 4)
 #undef BED_CASE
@@ -129,12 +131,22 @@ bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_
     bed_params prm;
     KParams kp;
     if (!make_kparams(p, &prm, &kp)) return BED_ERR_INVALID_ARG;
-    const int nmax = n <= 16 ? 16 : (n <= 32 ? 32 : 64);
+    // team shape: nmax rows of tiles, G lanes per row; the smallest nmax that holds n unless the caller
+    // asks for a thread count, which then selects the smallest (nmax >= n, G) with G * nmax equal to it
+    int nmax = n <= 16 ? 16 : (n <= 32 ? 32 : (n <= 48 ? 48 : 64));
     int g = 4;
     if (prm.threads_per_matrix != 0) {
-        if (prm.threads_per_matrix == 2 * nmax) g = 2;
-        else if (prm.threads_per_matrix == 4 * nmax) g = 4;
-        else return BED_ERR_INVALID_ARG;
+        bool found = false;
+        for (const int nm : {16, 32, 48, 64}) {
+            if (nm < n || found) continue;
+            for (const int gg : {4, 2})
+                if (!found && prm.threads_per_matrix == gg * nm) {
+                    nmax = nm;
+                    g = gg;
+                    found = true;
+                }
+        }
+        if (!found) return BED_ERR_INVALID_ARG;
     }
     if (batch == 0) return BED_OK;
     if (!A || !W || !V) return BED_ERR_INVALID_ARG;

@@ -140,7 +140,9 @@ __device__ __forceinline__ float sort_key(float x) { return isnan(x) ? INFINITY 
 template <int NMAX>
 __device__ __forceinline__ int yt_index(int i, int k)
 {
-    constexpr int SW = (NMAX / 4 < 8 ? NMAX / 4 : 8) - 1;
+    // XOR by at most 8 chunks, and by a divisor of the row's chunk count so that it stays in the row
+    constexpr int CH = NMAX / 4;
+    constexpr int SW = ((CH % 8 == 0) ? 8 : ((CH % 4 == 0) ? 4 : ((CH % 2 == 0) ? 2 : 1))) - 1;
     return i * NMAX + ((((k >> 2) ^ (i & SW)) << 2) | (k & 3));
 }
 

@@ -181,7 +181,14 @@ void launch(bed_server* s, int si, std::vector<Request*>& batch)
                                      sl.ws, sl.ws_bytes, nullptr, sl.stream);
         } else {
             Request* r = batch[0];
-            st = bed_eigh_f32(A + r->a_off, W + r->w_off, V + r->a_off, sl.info_d, r->b, r->n, &s->params, sl.stream);
+            bed_params p = s->params;
+            if (s->cfg.mode == 0) {
+                // the team shape and leaf size the ragged kernel gives this n, so that a request's results
+                // do not depend on whether it was batched with others (team t has 256 >> t threads)
+                p.threads_per_matrix = 256 >> s->tuning.team[r->n];
+                p.leaf_size = s->tuning.leaf[r->n];
+            }
+            st = bed_eigh_f32(A + r->a_off, W + r->w_off, V + r->a_off, sl.info_d, r->b, r->n, &p, sl.stream);
         }
     }
     k = 0;

@@ -183,3 +183,39 @@ def test_large_batch_sampled():
     idx = np.sort(rng.choice(b, 48, replace=False))
     Wo, Vo = run_oracle(A[idx])
     assert_parity(A[idx], W[idx], V[idx], info[idx], Wo, Vo, "sampled large batch")
+
+
+@pytest.mark.parametrize("tpm", [96, 192, 128, 256])
+def test_thread_count_selects_team_shape_n40(tpm):
+    """n = 40 runs on the 48-row team (96 or 192 threads) or, when asked, the 64-row team (128, 256):
+    every shape holds the tolerance."""
+    A = wl.covariance(48, 40, seed=33)
+    W, V, info = run_gpu(A, B.make_params(threads_per_matrix=tpm))
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W, V, info, Wo, Vo, f"n=40 threads={tpm}")
+
+
+def test_thread_count_rejects_shapes_below_n():
+    A = torch.from_numpy(wl.covariance(2, 40, seed=34)).cuda()
+    W = torch.empty(2, 40, device="cuda")
+    V = torch.empty(2, 40, 40, device="cuda")
+    for tpm in (64, 100, 2 * 32):  # 64 = 4 x 16 or 2 x 32: both below n = 40
+        st = B.bed_eigh_f32(A.data_ptr(), W.data_ptr(), V.data_ptr(), None, 2, 40,
+                            B.make_params(threads_per_matrix=tpm), torch.cuda.current_stream().cuda_stream)
+        assert st == B.BED_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_many_batches_on_streams_match_single_calls(where):
+    """batched_eigh_many runs each batch on its own stream; results are those of one call per batch."""
+    mats = [torch.from_numpy(wl.covariance(40, n, seed=60 + n)) for n in (64, 17, 48, 5, 32)]
+    if where == "device":
+        mats = [M.cuda() for M in mats]
+    many = B.batched_eigh_many(mats, return_info=True)
+    torch.cuda.synchronize()
+    for M, (W, V, info) in zip(mats, many):
+        W1, V1, info1 = B.batched_eigh(M, return_info=True)
+        torch.cuda.synchronize()
+        assert W.is_cuda == (where == "device")
+        assert torch.equal(W.cpu(), W1.cpu()) and torch.equal(V.cpu(), V1.cpu())
+        assert int((info != 0).sum()) == 0
