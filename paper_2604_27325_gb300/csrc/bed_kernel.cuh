@@ -46,7 +46,8 @@ struct Smem {
     float ds[NMAX], zs[NMAX];              // merge: poles and z in ascending pole order
     union alignas(16) {  // a1 and the merges never run at the same time
         struct {
-            float cd[NMAX], cz[NMAX], cz2[NMAX];  // merge: compacted (non-deflated first) scaled poles, z, z^2
+            float2 cdz[NMAX];  // merge: compacted (non-deflated first) scaled poles (x) and z^2 (y)
+            float cz[NMAX];    // merge: z in the compacted order
             float tq[NMAX], zh[NMAX];             // merge: root offsets from their poles, z-hat
             float rc[NMAX], rs[NMAX];             // merge: Givens deflation rotations (by sorted position)
         };
@@ -178,7 +179,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 
 // ---------------------------------------------------------------------------------------------
 // a5: one secular root (Eq. (8)) of the compacted, ascending, unit-scaled poles
-// d[0] < ... < d[K-1] with couplings z2[j] = z_j^2. Root q lies in (d_q, d_{q+1}) for q < K-1
+// d[0] < ... < d[K-1] with couplings z_j^2, stored as pairs dz[j] = (d[j], z_j^2). Root q lies in (d_q, d_{q+1}) for q < K-1
 // (Eq. (9)) and in (d_{K-1}, upper] for q = K-1 (Eq. (10)-(11)). Called by EVERY lane of the warp (non-participating lanes pass
 // part = false): the G lanes of a root split the pole sums and combine them with shuffles, and the
 // vote that retires the warp is taken by all 32 lanes.
@@ -191,9 +192,8 @@ struct RootOut {
 };
 
 template <int G>
-__device__ __forceinline__ RootOut secular_root(const float* __restrict__ d, const float* __restrict__ z2,
-                                                int K, int q, float rho, const KParams& kp, bool part,
-                                                int sub)
+__device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, int K, int q, float rho,
+                                                const KParams& kp, bool part, int sub)
 {
     RootOut r{q, 0.f, 0, false};
     bool done = !part;
@@ -205,11 +205,11 @@ __device__ __forceinline__ RootOut secular_root(const float* __restrict__ d, con
         float zn2 = 0.f, sd2 = 0.f, sdz = 0.f, sdza = 0.f;
         if (top)
             for (int j = sub; j < K; j += G) {
-                const float zz = z2[j];
-                zn2 += zz;
-                sd2 = fmaf(d[j], d[j], sd2);
-                sdz = fmaf(d[j], zz, sdz);
-                sdza = fmaf(fabsf(d[j]), zz, sdza);
+                const float2 p = dz[j];
+                zn2 += p.y;
+                sd2 = fmaf(p.x, p.x, sd2);
+                sdz = fmaf(p.x, p.y, sdz);
+                sdza = fmaf(fabsf(p.x), p.y, sdza);
             }
         zn2 = gsum<G>(zn2);
         sd2 = gsum<G>(sd2);
@@ -221,15 +221,16 @@ __device__ __forceinline__ RootOut secular_root(const float* __restrict__ d, con
             const float fro2 = fmaf(rz, rz, fmaf(2.f * rho, sdz, sd2));
             const float err2 = 4.f * (K + 4) * kU * fmaf(rz, rz, fmaf(2.f * rho, sdza, sd2));
             const float fro = sqrtf(fmaxf(fro2 + err2, 0.f));
-            const float uf = (fro - d[K - 1]) + 4.f * kU * (fro + fabsf(d[K - 1]));
+            const float dtop = dz[K - 1].x;
+            const float uf = (fro - dtop) + 4.f * kU * (fro + fabsf(dtop));
             if (uf > 0.f && uf < U) U = uf;
             if (K == 1) {  // one pole: 1 + rho z^2/(d - lambda) = 0 has lambda = d + rho z^2
-                r.tau = rho * z2[0];
+                r.tau = rho * dz[0].y;
                 r.conv = true;
                 done = true;
             }
         } else if (part) {
-            U = d[q + 1] - d[q];
+            U = dz[q + 1].x - dz[q].x;
         }
     }
     const float width0 = U;
@@ -246,19 +247,52 @@ __device__ __forceinline__ RootOut secular_root(const float* __restrict__ d, con
         const bool deriv = __any_sync(kFull, !done && state == 2);
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, sa = 0.f;
         if (!done) {
-            const float dorg = d[o];
+            const float dorg = dz[o].x;
+            // two poles per pass with separate partial sums (independent dependency chains)
             if (deriv) {
-                for (int j = sub; j < K; j += G) {
-                    const float inv = rcp_approx((d[j] - dorg) - h);
-                    const float t = z2[j] * inv;
-                    const float ti = t * inv;
-                    s0 += t;
-                    s1 += ti;
-                    s2 = fmaf(ti, inv, s2);
-                    sa += fabsf(t);
+                float s0b = 0.f, s1b = 0.f, s2b = 0.f, sab = 0.f;
+                int j = sub;
+                for (; j + G < K; j += 2 * G) {
+                    const float2 pa = dz[j], pb = dz[j + G];
+                    const float ia = rcp_approx((pa.x - dorg) - h), ib = rcp_approx((pb.x - dorg) - h);
+                    const float ta = pa.y * ia, tb = pb.y * ib;
+                    const float tia = ta * ia, tib = tb * ib;
+                    s0 += ta;
+                    s0b += tb;
+                    s1 += tia;
+                    s1b += tib;
+                    s2 = fmaf(tia, ia, s2);
+                    s2b = fmaf(tib, ib, s2b);
+                    sa += fabsf(ta);
+                    sab += fabsf(tb);
                 }
+                if (j < K) {
+                    const float2 pa = dz[j];
+                    const float ia = rcp_approx((pa.x - dorg) - h);
+                    const float ta = pa.y * ia;
+                    const float tia = ta * ia;
+                    s0 += ta;
+                    s1 += tia;
+                    s2 = fmaf(tia, ia, s2);
+                    sa += fabsf(ta);
+                }
+                s0 += s0b;
+                s1 += s1b;
+                s2 += s2b;
+                sa += sab;
             } else {
-                for (int j = sub; j < K; j += G) s0 = fmaf(z2[j], rcp_approx((d[j] - dorg) - h), s0);
+                float s0b = 0.f;
+                int j = sub;
+                for (; j + G < K; j += 2 * G) {
+                    const float2 pa = dz[j], pb = dz[j + G];
+                    s0 = fmaf(pa.y, rcp_approx((pa.x - dorg) - h), s0);
+                    s0b = fmaf(pb.y, rcp_approx((pb.x - dorg) - h), s0b);
+                }
+                if (j < K) {
+                    const float2 pa = dz[j];
+                    s0 = fmaf(pa.y, rcp_approx((pa.x - dorg) - h), s0);
+                }
+                s0 += s0b;
             }
         }
         s0 = gsum<G>(s0);
@@ -281,7 +315,7 @@ __device__ __forceinline__ RootOut secular_root(const float* __restrict__ d, con
             if (state == 0) {
                 if (!done && !top && f < 0.f) {
                     // root in the upper half of (d_q, d_{q+1}): measure it from d_{q+1}
-                    const float sh = d[q + 1] - d[q];
+                    const float sh = dz[q + 1].x - dz[q].x;
                     o = q + 1;
                     L -= sh;
                     U = 0.f;
@@ -794,9 +828,8 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             if (act && sub == 0) {
                 const int q = S.defl[t] ? (K + (t - lo - nb)) : nb;
                 S.inv[lo + q] = t;
-                S.cd[lo + q] = S.ds[t] * S.bsc[lb];
+                S.cdz[lo + q] = make_float2(S.ds[t] * S.bsc[lb], S.zs[t] * S.zs[t]);
                 S.cz[lo + q] = S.zs[t];
-                S.cz2[lo + q] = S.zs[t] * S.zs[t];
                 if (t == lo) {
                     S.bK[lb] = K;
                     atomicAdd(&S.deflated, static_cast<unsigned>(hi - lo - K));
@@ -815,19 +848,19 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 rho = S.brho[lb] * sc;
             }
             const bool part = act && (q < K);
-            const RootOut r = secular_root<G>(S.cd + lo, S.cz2 + lo, K, q, rho, kp, part, sub);
+            const RootOut r = secular_root<G>(S.cdz + lo, K, q, rho, kp, part, sub);
             if (sub == 0) {
                 if (part) {
                     S.org[lo + q] = lo + r.org;
                     S.tq[lo + q] = r.tau;
-                    S.lam[lo + q] = (S.cd[lo + r.org] + r.tau) * (1.f / sc);
+                    S.lam[lo + q] = (S.cdz[lo + r.org].x + r.tau) * (1.f / sc);
                     atomicAdd(&S.evals, static_cast<unsigned>(r.evals));
                     atomicAdd(&S.roots, 1u);
                     if (!r.conv) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
                 } else if (act) {
                     S.org[lo + q] = lo + q;
                     S.tq[lo + q] = 0.f;
-                    S.lam[lo + q] = S.cd[lo + q] * (1.f / sc);
+                    S.lam[lo + q] = S.cdz[lo + q].x * (1.f / sc);
                 }
             }
         }
@@ -842,12 +875,12 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             const bool own = act && (i < K);
             float prod = 1.f;
             if (own) {
-                const float di = S.cd[lo + i];
+                const float di = S.cdz[lo + i].x;
                 if (sub == 0)
-                    prod = ((S.cd[S.org[lo + K - 1]] - di) + S.tq[lo + K - 1]) / (S.brho[lb] * S.bsc[lb]);
+                    prod = ((S.cdz[S.org[lo + K - 1]].x - di) + S.tq[lo + K - 1]) / (S.brho[lb] * S.bsc[lb]);
                 for (int j = sub; j < K - 1; j += G) {
-                    const float num = (S.cd[S.org[lo + j]] - di) + S.tq[lo + j];  // lambda_j - d_i
-                    const float den = (j < i) ? (S.cd[lo + j] - di) : (S.cd[lo + j + 1] - di);
+                    const float num = (S.cdz[S.org[lo + j]].x - di) + S.tq[lo + j];  // lambda_j - d_i
+                    const float den = (j < i) ? (S.cdz[lo + j].x - di) : (S.cdz[lo + j + 1].x - di);
                     prod *= num / den;
                 }
             }
@@ -864,10 +897,10 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             float nrm2 = 0.f;
             if (act) {
                 if (q < K) {
-                    const float dorg = S.cd[S.org[lo + q]];
+                    const float dorg = S.cdz[S.org[lo + q]].x;
                     const float tq = S.tq[lo + q];
                     for (int i = sub; i < K; i += G) {
-                        const float v = __fdividef(S.zh[lo + i], (S.cd[lo + i] - dorg) - tq);
+                        const float v = __fdividef(S.zh[lo + i], (S.cdz[lo + i].x - dorg) - tq);
                         S.M[S.inv[lo + i] * LD + cq] = v;
                         nrm2 = fmaf(v, v, nrm2);
                     }
