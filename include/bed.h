@@ -63,7 +63,7 @@ typedef struct {
     int k_multisection;      /* k of Eq. (16), >= 2 (default 4) */
     int max_section_iters;   /* cap on multi-section steps per root, 0..256 (default 24) */
     int max_halley_iters;    /* cap on Halley steps per root, 1..256 (default 32) */
-    float section_rel_eps;   /* Eq. (17): sectioning stops when U - L < eps * (initial bracket), (0,1) (default 2^-2) */
+    float section_rel_eps;   /* Eq. (17): sectioning stops when U - L < eps * (initial bracket), (0,1) (default 2^-1) */
     float stop_c;            /* Halley stops when |f| <= stop_c * u * (1 + rho sum|z^2/(d - lambda)|), u = 2^-24 (default 8) */
     float deflation_tol_scale; /* deflation tolerance = scale * u * max(max|d|, rho |z|^2) (default 8) */
     int threads_per_matrix;  /* 0 = automatic (4*nmax, nmax the smallest of {16, 32, 48, 64} that holds n);

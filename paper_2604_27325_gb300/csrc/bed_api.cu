@@ -232,7 +232,7 @@ void bed_default_params(bed_params* p)
     p->k_multisection = 4;
     p->max_section_iters = 24;
     p->max_halley_iters = 32;
-    p->section_rel_eps = 0x1p-2f;
+    p->section_rel_eps = 0x1p-1f;
     p->stop_c = 8.f;
     p->deflation_tol_scale = 8.f;
     p->threads_per_matrix = 0;

@@ -349,7 +349,21 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
                     const float den = 2.f * f1 * f1 - f * f2;
                     float hn = h - 2.f * f * f1 / den;  // Eq. (20)
                     const bool inside = (hn > L) && (top ? hn <= U : hn < U);
-                    if (!(den > 0.f) || !inside) hn = 0.5f * (L + U);
+                    if (!(den > 0.f) || !inside) {
+                        // Halley's step left the bracket: far from a root that hugs its pole d_o, f is
+                        // nearly flat. Write f = rho z_o^2 / (d_o - lambda) + g with the rest g taken
+                        // constant at its value here; the root of that model, h = rho z_o^2 / g, is the
+                        // next iterate when it lies inside the bracket, else the midpoint.
+                        hn = 0.5f * (L + U);
+                        if (h != 0.f) {
+                            const float rz = rho * dz[o].y;
+                            const float g = f + rz / h;
+                            if (g != 0.f) {
+                                const float he = rz / g;
+                                if ((he > L) && (top ? he <= U : he < U)) hn = he;
+                            }
+                        }
+                    }
                     if (fabsf(hn - h) <= 4.f * kU * fabsf(hn)) {
                         done = true;
                         r.conv = true;

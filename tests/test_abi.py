@@ -37,7 +37,7 @@ def test_constants_and_strings():
     assert C.sizeof(B.bed_counters) == 32
     p = B.bed_default_params()
     assert (p.leaf_size, p.k_multisection, p.retire_by_vote, p.threads_per_matrix) == (2, 4, 1, 0)
-    assert p.section_rel_eps == 2.0**-2
+    assert p.section_rel_eps == 2.0**-1
 
 
 FAKE = 1 << 20  # aligned, never dereferenced: every call below is rejected before a launch
