@@ -3,8 +3,8 @@
 // One thread block solves one matrix at a time, entirely in shared memory:
 //   a0  stage A[b] into shared memory (TMA bulk copy + mbarrier, or coalesced loads), read the lower
 //       triangle, check finiteness, scale by a power of two
-//   a1  Householder tridiagonalization: reflector norms and p.v by warp shuffles, the matvec split
-//       over G lanes per row, two block barriers per reflector
+//   a1  Householder tridiagonalization: A in column-owned register tiles, p = tau A v from the
+//       column sums of each warp's block (A is symmetric), one block barrier per reflector
 //   a2  tear the tridiagonal along the static divide tree (Sec. 2.1, Eq. (2)-(3))
 //   a3  2x2 leaves by one Jacobi rotation (Sec. 2.2)
 //   a4  per merge (Eq. (4)-(5)): coupling vector z, pole ordering, deflation
@@ -12,13 +12,13 @@
 //       relative to the nearer pole; a warp stops iterating when all of its lanes have converged
 //       (the GPU form of the progressive batch shrinkage, Eq. (22))
 //   a6  Gu-Eisenstat z-hat (Eq. (25)) and normalized eigenvectors (Eq. (24))
-//   a7  merge GEMM Q <- blkdiag(Q1, Q2) Q^ (Eq. (4))
-//   a8  back-transform through the Householder reflectors, 8 at a time as I - Y T Y^T
+//   a7  merge GEMM Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)) in register tiles of 4 rows x 16/G columns
+//   a8  back-transform through the Householder reflectors, 8 at a time as I - Y T Y^T, with each
+//       column of Q held in the registers of its G lanes
 //   a9  ascending order, sign convention, store
-// Thread layouts (NT = NMAX * G threads):
-//   "position" pos = tid / G, sub = tid % G: G consecutive lanes share one row / column / root and
-//       combine their partial results with shuffles inside the group;
-//   "column"   col = tid % NMAX, grp = tid / NMAX: used by the rank updates and GEMM-like phases.
+// Thread layouts (NT = NMAX * G threads): "position" pos = tid / G, sub = tid % G: G consecutive
+// lanes share one row / column / root and combine their partial results with shuffles inside the
+// group; a1 and a7 use their own register tilings, described where they run.
 #pragma once
 
 #include <cfloat>
@@ -39,8 +39,10 @@ struct Smem {
     static constexpr int LD = NMAX + 1;  // odd stride: column walks hit distinct banks
     static constexpr int NB = NMAX / 2;  // merges per level, at most
     alignas(16) float A[NMAX * LD];  // matrix; after a1 the reflectors, transposed (yt_index)
-    float Q[NMAX * LD];  // eigenvectors of the current blocks (block diagonal)
-    alignas(16) float M[NMAX * LD];  // staging of A[b]; merge workspace (rows = sorted poles); a8 workspace
+    float Q[NMAX * LD + 3 * LD];      // eigenvectors of the current blocks (block diagonal); P8 tiles read
+                                      // up to 3 rows past the last one
+    alignas(16) float M[NMAX * LD + 8];  // staging of A[b]; merge workspace (rows = sorted poles); a8
+                                         // workspace; P8 tiles read up to 7 columns past the last one
     float d[NMAX], e[NMAX], tau[NMAX];     // tridiagonal and reflector scalars
     float lam[NMAX];                       // eigenvalue of each column of Q
     float ds[NMAX], zs[NMAX];              // merge: poles and z in ascending pole order
@@ -130,6 +132,52 @@ __device__ __forceinline__ float rcp_approx(float x)
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// Vector shared-memory access of N consecutive floats (16- or 8-byte aligned when N is 4, 8 or 2).
+template <int N>
+__device__ __forceinline__ void load_vec(const float* p, float (&v)[N])
+{
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 t = reinterpret_cast<const float4*>(p)[q];
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+    } else if constexpr (N == 2) {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        v[0] = t.x;
+        v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) v[q] = p[q];
+    }
+}
+template <int N>
+__device__ __forceinline__ void store_vec(float* p, const float (&v)[N])
+{
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q)
+            reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if constexpr (N == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) p[q] = v[q];
+    }
+}
+
+// Sum over the 16 lanes that share lane bit 0 (the row lanes of the a1 tile layout); all of them get
+// the same value.
+__device__ __forceinline__ float row_lane_sum(float v)
+{
+#pragma unroll
+    for (int o = 2; o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
 }
 
 // Sort key with a total order: NaN sorts last, ties broken by index by the callers.
@@ -405,11 +453,8 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
     constexpr int NT = NMAX * G;
     constexpr int NW = NT / 32;
     constexpr int LD = Smem<NMAX, G>::LD;
-    constexpr int RPT = NMAX / G;  // rows per thread in the column layout
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    const int col = tid % NMAX;
-    const int grp = tid / NMAX;
     const int pos = tid / G;
     const int sub = tid % G;
     const int n = plan.n;
@@ -498,13 +543,13 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
     // only. Step k reads three vectors that step k-1 left in shared memory (double-buffered by step
     // parity): p_{k-1}, v_{k-1} and column k of A before the update of step k-1. From them every warp
     // forms, redundantly and identically, w_{k-1} = p - (tau/2)(p.v) v, column k of the updated matrix
-    // and reflector k; it applies A22 -= v w^T + w v^T of step k-1 to its tile and forms the column
-    // sums with v_k. A warp whose columns are all finished skips the step.
+    // and reflector k (each warp holds every row, so the sums over rows are shuffle sums over its row
+    // lanes); it applies A22 -= v w^T + w v^T of step k-1 to its tile and forms the column sums with
+    // v_k. A warp whose columns are all finished skips the step.
     {
         constexpr int WC = NMAX / NW;             // columns per warp
         constexpr int TC = WC / 2;                // tile columns per lane
         constexpr int TR = NMAX / 16;             // tile rows per lane
-        constexpr int NL = (NMAX + 31) / 32;      // entries per lane in the lane layout i = lane + 32 m
         constexpr int LOG_TC = (TC == 8) ? 3 : (TC == 4 ? 2 : (TC == 2 ? 1 : 0));
         static_assert(WC * NW == NMAX && TR * 16 == NMAX && (1 << LOG_TC) == TC, "tile shape");
         const int tr = lane >> 1, tc = lane & 1;
@@ -535,57 +580,57 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             const float* Yr = S.hy[(k + 1) & 1];
             float tau = 0.f;
             if (warp * WC + WC > k + 1 && warp <= wlast) {
-                // c = (tau/2) p.v of step k - 1, in the lane layout
+                // the three vectors on this lane's rows; every warp holds all NMAX rows, so sums over
+                // rows are sums over the 16 row lanes (the two column lanes of a row agree)
+                float pr[TR], ur[TR], yr[TR];
+                load_vec<TR>(Pr + i0, pr);
+                load_vec<TR>(Ur + i0, ur);
+                load_vec<TR>(Yr + i0, yr);
                 float dot = 0.f;
 #pragma unroll
-                for (int m = 0; m < NL; ++m) {
-                    const int i = lane + 32 * m;
-                    if (i < NMAX) dot = fmaf(Pr[i], Ur[i], dot);
-                }
-                const float c = 0.5f * tau_prev * warp_sum(dot);
+                for (int ii = 0; ii < TR; ++ii) dot = fmaf(pr[ii], ur[ii], dot);
+                const float c = 0.5f * tau_prev * row_lane_sum(dot);  // (tau/2) p.v of step k - 1
                 const float uk = Ur[k];
                 const float wk = fmaf(-c, uk, Pr[k]);
-                // x = column k of the updated matrix, rows k + 1 ..
+                // w of step k - 1 (zero on finished rows) and x = column k of the updated matrix
+                float wr[TR], xr[TR];
                 float part = 0.f;
-                float xl[NL];
 #pragma unroll
-                for (int m = 0; m < NL; ++m) {
-                    const int i = lane + 32 * m;
-                    xl[m] = 0.f;
-                    if (i < NMAX) {
-                        const float u = Ur[i];
-                        xl[m] = fmaf(-fmaf(-c, u, Pr[i]), uk, fmaf(-u, wk, Yr[i]));
-                    }
-                    if (i > k + 1 && i < n) part = fmaf(xl[m], xl[m], part);
+                for (int ii = 0; ii < TR; ++ii) {
+                    const int i = i0 + ii;
+                    const float w = fmaf(-c, ur[ii], pr[ii]);
+                    wr[ii] = (i >= k) ? w : 0.f;
+                    xr[ii] = fmaf(-w, uk, fmaf(-ur[ii], wk, yr[ii]));
+                    if (i > k + 1 && i < n) part = fmaf(xr[ii], xr[ii], part);
                 }
-                const float xn2 = warp_sum(part);
+                const float xn2 = row_lane_sum(part);
                 const float u1 = Ur[k + 1];
                 const float alpha = fmaf(-fmaf(-c, u1, Pr[k + 1]), uk, fmaf(-u1, wk, Yr[k + 1]));
                 float beta = alpha, scal = 0.f;
                 if (xn2 > 0.f) {
                     const float nrm = sqrtf(fmaf(alpha, alpha, xn2));
                     beta = (alpha >= 0.f) ? -nrm : nrm;
-                    tau = (beta - alpha) / beta;
-                    scal = 1.f / (alpha - beta);
+                    // |beta| = nrm and |alpha - beta| >= nrm: both normal, far from overflow
+                    tau = (beta - alpha) * rcp_approx(beta);
+                    scal = rcp_approx(alpha - beta);
                 }
-                // update of step k - 1 on the tile (rows and columns >= k), then the column sums of
-                // the updated tile with v_k
-                float ur[TR], wr[TR], vr[TR];
+                float vr[TR];
 #pragma unroll
                 for (int ii = 0; ii < TR; ++ii) {
                     const int i = i0 + ii;
-                    const float u = Ur[i], p = Pr[i];
-                    ur[ii] = u;
-                    wr[ii] = (i >= k) ? fmaf(-c, u, p) : 0.f;
-                    const float x = fmaf(-fmaf(-c, u, p), uk, fmaf(-u, wk, Yr[i]));
-                    vr[ii] = (i > k + 1) ? x * scal : ((i == k + 1) ? 1.f : 0.f);
+                    vr[ii] = (i > k + 1) ? xr[ii] * scal : ((i == k + 1) ? 1.f : 0.f);
                 }
+                // update of step k - 1 on the tile (rows and columns >= k), then the column sums of
+                // the updated tile with v_k
+                float pc[TC], uc[TC];
+                load_vec<TC>(Pr + j0, pc);
+                load_vec<TC>(Ur + j0, uc);
                 float s[TC];
 #pragma unroll
                 for (int jj = 0; jj < TC; ++jj) {
                     const int j = j0 + jj;
-                    const float u = Ur[j];
-                    const float w = (j >= k) ? fmaf(-c, u, Pr[j]) : 0.f;
+                    const float u = uc[jj];
+                    const float w = (j >= k) ? fmaf(-c, u, pc[jj]) : 0.f;
                     float acc = 0.f;
 #pragma unroll
                     for (int ii = 0; ii < TR; ++ii) {
@@ -617,26 +662,21 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 // column k + 1 of the updated matrix, for step k + 1
                 if (warp == (k + 1) / WC && tc == ((k + 1) % WC) / TC) {
                     const int kj = (k + 1) % TC;
-                    float* Yw = S.hy[k & 1];
+                    float yk[TR];
 #pragma unroll
                     for (int ii = 0; ii < TR; ++ii) {
                         float x = 0.f;
 #pragma unroll
                         for (int jj = 0; jj < TC; ++jj) x = (jj == kj) ? a[ii][jj] : x;
-                        Yw[i0 + ii] = x;
+                        yk[ii] = x;
                     }
+                    store_vec<TR>(S.hy[k & 1] + i0, yk);
                 }
-                if (warp == wlast) {
-                    float* Uw = S.hu[k & 1];
+                // reflector k: for the next step and, transposed, for the back-transform
+                if (warp == wlast && tc == 0) {
+                    store_vec<TR>(S.hu[k & 1] + i0, vr);
 #pragma unroll
-                    for (int m = 0; m < NL; ++m) {
-                        const int i = lane + 32 * m;
-                        if (i < NMAX) {
-                            const float v = (i > k + 1 && i < n) ? xl[m] * scal : ((i == k + 1) ? 1.f : 0.f);
-                            Uw[i] = v;
-                            S.A[yt_index<NMAX>(i, k)] = v;
-                        }
-                    }
+                    for (int ii = 0; ii < TR; ++ii) S.A[yt_index<NMAX>(i0 + ii, k)] = vr[ii];
                     if (lane == 0) {
                         S.d[k] = fmaf(-2.f * uk, wk, Yr[k]);
                         S.e[k] = beta;
@@ -659,11 +699,8 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             const float* Ur = S.hu[(kf + 1) & 1];
             float dot = 0.f;
 #pragma unroll
-            for (int m = 0; m < NL; ++m) {
-                const int i = lane + 32 * m;
-                if (i < NMAX) dot = fmaf(Pr[i], Ur[i], dot);
-            }
-            const float c = 0.5f * tau_prev * warp_sum(dot);
+            for (int ii = 0; ii < TR; ++ii) dot = fmaf(Pr[i0 + ii], Ur[i0 + ii], dot);
+            const float c = 0.5f * tau_prev * row_lane_sum(dot);
 #pragma unroll
             for (int ii = 0; ii < TR; ++ii)
 #pragma unroll
@@ -944,34 +981,67 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             }
         }
         team_sync<NT>(bar_id);
-        // P8: Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)); rows of Q^ are gathered through the pole order
+        // P8: Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)); rows of Q^ are gathered through the pole order.
+        // Register tiles: the rows of one half of a merge times its columns form a small product over
+        // the half's columns c. The level's tiles (PR rows x PC columns, merges in order, row tiles of
+        // the left half, then of the right half, each with all column tiles) are dealt one per thread;
+        // per c a thread reads PR entries of Q, one row of Q^ (PC entries) and does PR x PC FMAs.
         {
-            const int bc = (col < n) ? plan.blk[L][col] : 0xFF;
-            float acc[RPT];
-            int clo = 0, cmid = 0, chi = 0;
-            if (bc != 0xFF) {
-                clo = plan.m_lo[bc];
-                cmid = plan.m_mid[bc];
-                chi = plan.m_hi[bc];
+            constexpr int PR = 4;
+            constexpr int PC = 16 / G;
+            int r0 = 0, rend = 0, c0 = 0, c1 = 0, q0 = 0, qend = 0;
+            bool have = false;
+            {
+                int tbase = 0;
+                for (int m = plan.level_start[L]; m < plan.level_start[L + 1]; ++m) {
+                    const int lo = plan.m_lo[m], md = plan.m_mid[m], hi = plan.m_hi[m];
+                    const int rtl = (md - lo + PR - 1) / PR, rtr = (hi - md + PR - 1) / PR;
+                    const int ctn = (hi - lo + PC - 1) / PC;
+                    const int cnt = (rtl + rtr) * ctn;
+                    if (tid >= tbase && tid < tbase + cnt) {
+                        const int u = tid - tbase;
+                        const int rr = u / ctn, ct = u - rr * ctn;
+                        const bool left = rr < rtl;
+                        r0 = left ? lo + PR * rr : md + PR * (rr - rtl);
+                        rend = left ? md : hi;
+                        c0 = left ? lo : md;
+                        c1 = left ? md : hi;
+                        q0 = lo + PC * ct;
+                        qend = hi;
+                        have = true;
+                    }
+                    tbase += cnt;
+                }
+            }
+            float acc[PR][PC];
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) acc[k] = 0.f;
-                for (int c = clo; c < chi; ++c) {
-                    const float mv = S.M[S.rank[c] * LD + col];
-                    const bool left = c < cmid;
+            for (int i = 0; i < PR; ++i)
 #pragma unroll
-                    for (int k = 0; k < RPT; ++k) {
-                        const int r = clo + grp + G * k;
-                        if (r < chi && ((r < cmid) == left)) acc[k] = fmaf(S.Q[r * LD + c], mv, acc[k]);
+                for (int j = 0; j < PC; ++j) acc[i][j] = 0.f;
+            if (have) {
+                // rows past rend and columns past qend read padding or neighbouring entries; their
+                // sums are never stored
+                const float* qrow = S.Q + r0 * LD;
+                for (int c = c0; c < c1; ++c) {
+                    const float* mrow = S.M + S.rank[c] * LD + q0;
+                    float mv[PC];
+#pragma unroll
+                    for (int j = 0; j < PC; ++j) mv[j] = mrow[j];
+#pragma unroll
+                    for (int i = 0; i < PR; ++i) {
+                        const float qv = qrow[i * LD + c];
+#pragma unroll
+                        for (int j = 0; j < PC; ++j) acc[i][j] = fmaf(qv, mv[j], acc[i][j]);
                     }
                 }
             }
             team_sync<NT>(bar_id);
-            if (bc != 0xFF) {
+            if (have) {
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) {
-                    const int r = clo + grp + G * k;
-                    if (r < chi) S.Q[r * LD + col] = acc[k];
-                }
+                for (int i = 0; i < PR; ++i)
+#pragma unroll
+                    for (int j = 0; j < PC; ++j)
+                        if (r0 + i < rend && q0 + j < qend) S.Q[(r0 + i) * LD + q0 + j] = acc[i][j];
             }
         }
         team_sync<NT>(bar_id);
