@@ -603,40 +603,66 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                     xr[ii] = fmaf(-w, uk, fmaf(-ur[ii], wk, yr[ii]));
                     if (i > k + 1 && i < n) part = fmaf(xr[ii], xr[ii], part);
                 }
+                // the update of step k - 1 needs only c: apply it to the tile (rows and columns >= k)
+                // while the reduction for reflector k is in flight
+                float pc[TC], uc[TC];
+                load_vec<TC>(Pr + j0, pc);
+                load_vec<TC>(Ur + j0, uc);
+#pragma unroll
+                for (int jj = 0; jj < TC; ++jj) {
+                    const int j = j0 + jj;
+                    const float u = uc[jj];
+                    const float w = (j >= k) ? fmaf(-c, u, pc[jj]) : 0.f;
+#pragma unroll
+                    for (int ii = 0; ii < TR; ++ii) a[ii][jj] = fmaf(-ur[ii], w, fmaf(-wr[ii], u, a[ii][jj]));
+                }
+                // column k + 1 of the updated matrix, for step k + 1
+                if (warp == (k + 1) / WC && tc == ((k + 1) % WC) / TC) {
+                    const int kj = (k + 1) % TC;
+                    float yk[TR];
+#pragma unroll
+                    for (int ii = 0; ii < TR; ++ii) {
+                        float x = 0.f;
+#pragma unroll
+                        for (int jj = 0; jj < TC; ++jj) x = (jj == kj) ? a[ii][jj] : x;
+                        yk[ii] = x;
+                    }
+                    store_vec<TR>(S.hy[k & 1] + i0, yk);
+                }
                 const float xn2 = row_lane_sum(part);
                 const float u1 = Ur[k + 1];
                 const float alpha = fmaf(-fmaf(-c, u1, Pr[k + 1]), uk, fmaf(-u1, wk, Yr[k + 1]));
-                float beta = alpha, scal = 0.f;
-                if (xn2 > 0.f) {
-                    const float nrm = sqrtf(fmaf(alpha, alpha, xn2));
-                    beta = (alpha >= 0.f) ? -nrm : nrm;
-                    // |beta| = nrm and |alpha - beta| >= nrm: both normal, far from overflow
-                    tau = (beta - alpha) * rcp_approx(beta);
-                    scal = rcp_approx(alpha - beta);
-                }
+                // reflector k; when x is already zero below its first entry, tau = 0 and beta = alpha.
+                // |beta| = nrm and |alpha - beta| >= nrm: both normal, far from overflow
+                const float nrm = sqrtf(fmaf(alpha, alpha, xn2));
+                const bool refl = xn2 > 0.f;
+                const float beta = refl ? ((alpha >= 0.f) ? -nrm : nrm) : alpha;
+                tau = refl ? (beta - alpha) * rcp_approx(beta) : 0.f;
+                const float scal = refl ? rcp_approx(alpha - beta) : 0.f;
                 float vr[TR];
 #pragma unroll
                 for (int ii = 0; ii < TR; ++ii) {
                     const int i = i0 + ii;
                     vr[ii] = (i > k + 1) ? xr[ii] * scal : ((i == k + 1) ? 1.f : 0.f);
                 }
-                // update of step k - 1 on the tile (rows and columns >= k), then the column sums of
-                // the updated tile with v_k
-                float pc[TC], uc[TC];
-                load_vec<TC>(Pr + j0, pc);
-                load_vec<TC>(Ur + j0, uc);
+                // reflector k: for the next step and, transposed, for the back-transform
+                if (warp == wlast && tc == 0) {
+                    store_vec<TR>(S.hu[k & 1] + i0, vr);
+#pragma unroll
+                    for (int ii = 0; ii < TR; ++ii) S.A[yt_index<NMAX>(i0 + ii, k)] = vr[ii];
+                    if (lane == 0) {
+                        S.d[k] = fmaf(-2.f * uk, wk, Yr[k]);
+                        S.e[k] = beta;
+                        S.tau[k] = tau;
+                    }
+                }
+                // column sums of the updated tile with v_k
                 float s[TC];
 #pragma unroll
                 for (int jj = 0; jj < TC; ++jj) {
-                    const int j = j0 + jj;
-                    const float u = uc[jj];
-                    const float w = (j >= k) ? fmaf(-c, u, pc[jj]) : 0.f;
                     float acc = 0.f;
 #pragma unroll
-                    for (int ii = 0; ii < TR; ++ii) {
-                        a[ii][jj] = fmaf(-ur[ii], w, fmaf(-wr[ii], u, a[ii][jj]));
-                        acc = fmaf(a[ii][jj], vr[ii], acc);
-                    }
+                    for (int ii = 0; ii < TR; ++ii) acc = fmaf(a[ii][jj], vr[ii], acc);
                     s[jj] = acc;
                 }
                 // sum over the 16 row lanes: halving exchanges leave lane bits 1.. LOG_TC holding one
@@ -659,30 +685,6 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 for (int o = 2 << LOG_TC; o < 32; o <<= 1) s[0] += __shfl_xor_sync(kFull, s[0], o);
                 float* Pw = S.hp[k & 1];
                 if ((lane >> (1 + LOG_TC)) == 0) Pw[j0 + cb] = tau * s[0];
-                // column k + 1 of the updated matrix, for step k + 1
-                if (warp == (k + 1) / WC && tc == ((k + 1) % WC) / TC) {
-                    const int kj = (k + 1) % TC;
-                    float yk[TR];
-#pragma unroll
-                    for (int ii = 0; ii < TR; ++ii) {
-                        float x = 0.f;
-#pragma unroll
-                        for (int jj = 0; jj < TC; ++jj) x = (jj == kj) ? a[ii][jj] : x;
-                        yk[ii] = x;
-                    }
-                    store_vec<TR>(S.hy[k & 1] + i0, yk);
-                }
-                // reflector k: for the next step and, transposed, for the back-transform
-                if (warp == wlast && tc == 0) {
-                    store_vec<TR>(S.hu[k & 1] + i0, vr);
-#pragma unroll
-                    for (int ii = 0; ii < TR; ++ii) S.A[yt_index<NMAX>(i0 + ii, k)] = vr[ii];
-                    if (lane == 0) {
-                        S.d[k] = fmaf(-2.f * uk, wk, Yr[k]);
-                        S.e[k] = beta;
-                        S.tau[k] = tau;
-                    }
-                }
             }
             tau_prev = tau;
             team_sync<NT>(bar_id);
