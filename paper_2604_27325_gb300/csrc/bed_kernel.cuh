@@ -171,13 +171,23 @@ __device__ __forceinline__ void store_vec(float* p, const float (&v)[N])
     }
 }
 
-// Sum over the 16 lanes that share lane bit 0 (the row lanes of the a1 tile layout); all of them get
-// the same value.
+// Sum over the 32 / NTC lanes that share lane % NTC (the row lanes of the a1 tile layout); all of
+// them get the same value.
+template <int NTC>
 __device__ __forceinline__ float row_lane_sum(float v)
 {
 #pragma unroll
-    for (int o = 2; o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+    for (int o = NTC; o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
+}
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+// Lanes along the columns of a warp's block in the a1 tile layout (the rest run along the rows).
+template <int NMAX, int G>
+__host__ __device__ constexpr int a1_col_lanes()
+{
+    return 2;
 }
 
 // Sort key with a total order: NaN sorts last, ties broken by index by the callers.
@@ -395,7 +405,7 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
                     done = true;  // not converged: keep the last iterate
                 } else {
                     const float den = 2.f * f1 * f1 - f * f2;
-                    float hn = h - 2.f * f * f1 / den;  // Eq. (20)
+                    float hn = h - (2.f * f * f1) * rcp_approx(den);  // Eq. (20)
                     const bool inside = (hn > L) && (top ? hn <= U : hn < U);
                     if (!(den > 0.f) || !inside) {
                         // Halley's step left the bracket: far from a root that hugs its pole d_o, f is
@@ -537,7 +547,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
 
     // ---------------- a1: Householder tridiagonalization ------------------------------------
     // Column-owned register tiles, one barrier per reflector. Warp w keeps columns
-    // [w WC, (w + 1) WC) of A in registers: lane (tr, tc) = (lane >> 1, lane & 1) holds rows
+    // [w WC, (w + 1) WC) of A in registers: lane (tr, tc) = (lane / NTC, lane % NTC) holds rows
     // [TR tr, TR tr + TR) of columns w WC + TC tc + [0, TC). A is symmetric, so the column sums of a
     // warp's block are the entries of A v at its columns: p = tau A22 v needs shuffles inside the warp
     // only. Step k reads three vectors that step k-1 left in shared memory (double-buffered by step
@@ -548,11 +558,16 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
     // v_k. A warp whose columns are all finished skips the step.
     {
         constexpr int WC = NMAX / NW;             // columns per warp
-        constexpr int TC = WC / 2;                // tile columns per lane
-        constexpr int TR = NMAX / 16;             // tile rows per lane
-        constexpr int LOG_TC = (TC == 8) ? 3 : (TC == 4 ? 2 : (TC == 2 ? 1 : 0));
-        static_assert(WC * NW == NMAX && TR * 16 == NMAX && (1 << LOG_TC) == TC, "tile shape");
-        const int tr = lane >> 1, tc = lane & 1;
+        constexpr int NTC = a1_col_lanes<NMAX, G>();  // lanes along the columns
+        constexpr int NTR = 32 / NTC;             // lanes along the rows
+        constexpr int TC = WC / NTC;              // tile columns per lane
+        constexpr int TR = NMAX / NTR;            // tile rows per lane
+        constexpr int LOG_TC = ilog2(TC);
+        constexpr int LOG_NTC = ilog2(NTC);
+        static_assert(WC * NW == NMAX && TR * NTR == NMAX && TC * NTC == WC && (1 << LOG_TC) == TC &&
+                          (1 << LOG_NTC) == NTC,
+                      "tile shape");
+        const int tr = lane / NTC, tc = lane % NTC;
         const int i0 = tr * TR, j0 = warp * WC + tc * TC;
         float a[TR][TC];
 #pragma unroll
@@ -589,7 +604,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 float dot = 0.f;
 #pragma unroll
                 for (int ii = 0; ii < TR; ++ii) dot = fmaf(pr[ii], ur[ii], dot);
-                const float c = 0.5f * tau_prev * row_lane_sum(dot);  // (tau/2) p.v of step k - 1
+                const float c = 0.5f * tau_prev * row_lane_sum<NTC>(dot);  // (tau/2) p.v of step k - 1
                 const float uk = Ur[k];
                 const float wk = fmaf(-c, uk, Pr[k]);
                 // w of step k - 1 (zero on finished rows) and x = column k of the updated matrix
@@ -629,7 +644,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                     }
                     store_vec<TR>(S.hy[k & 1] + i0, yk);
                 }
-                const float xn2 = row_lane_sum(part);
+                const float xn2 = row_lane_sum<NTC>(part);
                 const float u1 = Ur[k + 1];
                 const float alpha = fmaf(-fmaf(-c, u1, Pr[k + 1]), uk, fmaf(-u1, wk, Yr[k + 1]));
                 // reflector k; when x is already zero below its first entry, tau = 0 and beta = alpha.
@@ -665,13 +680,13 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                     for (int ii = 0; ii < TR; ++ii) acc = fmaf(a[ii][jj], vr[ii], acc);
                     s[jj] = acc;
                 }
-                // sum over the 16 row lanes: halving exchanges leave lane bits 1.. LOG_TC holding one
-                // column each, plain butterflies finish the sum
+                // sum over the row lanes: halving exchanges leave the lowest LOG_TC row-lane bits
+                // holding one column each, plain butterflies finish the sum
                 int cb = 0;
 #pragma unroll
                 for (int l = 0; l < LOG_TC; ++l) {
                     const int h = TC >> (l + 1);
-                    const int o = 2 << l;
+                    const int o = NTC << l;
                     const bool up = (lane & o) != 0;
 #pragma unroll
                     for (int t = 0; t < h; ++t) {
@@ -682,9 +697,9 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                     if (up) cb += h;
                 }
 #pragma unroll
-                for (int o = 2 << LOG_TC; o < 32; o <<= 1) s[0] += __shfl_xor_sync(kFull, s[0], o);
+                for (int o = NTC << LOG_TC; o < 32; o <<= 1) s[0] += __shfl_xor_sync(kFull, s[0], o);
                 float* Pw = S.hp[k & 1];
-                if ((lane >> (1 + LOG_TC)) == 0) Pw[j0 + cb] = tau * s[0];
+                if ((lane >> (LOG_NTC + LOG_TC)) == 0) Pw[j0 + cb] = tau * s[0];
             }
             tau_prev = tau;
             team_sync<NT>(bar_id);
@@ -702,7 +717,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             float dot = 0.f;
 #pragma unroll
             for (int ii = 0; ii < TR; ++ii) dot = fmaf(Pr[i0 + ii], Ur[i0 + ii], dot);
-            const float c = 0.5f * tau_prev * row_lane_sum(dot);
+            const float c = 0.5f * tau_prev * row_lane_sum<NTC>(dot);
 #pragma unroll
             for (int ii = 0; ii < TR; ++ii)
 #pragma unroll
@@ -931,8 +946,19 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 const float di = S.cdz[lo + i].x;
                 if (sub == 0)
                     prod = ((S.cdz[S.org[lo + K - 1]].x - di) + S.tq[lo + K - 1]) / (S.brho[lb] * S.bsc[lb]);
-                for (int j = sub; j < K - 1; j += G) {
-                    const float num = (S.cdz[S.org[lo + j]].x - di) + S.tq[lo + j];  // lambda_j - d_i
+                // two ratios per division: their indices differ by G >= 2, so at most one of the two
+                // numerators is a root hugging d_i, and both products stay far inside the FP32 range
+                int j = sub;
+                for (; j + G < K - 1; j += 2 * G) {
+                    const int jb = j + G;
+                    const float na = (S.cdz[S.org[lo + j]].x - di) + S.tq[lo + j];  // lambda_j - d_i
+                    const float nb = (S.cdz[S.org[lo + jb]].x - di) + S.tq[lo + jb];
+                    const float da = (j < i) ? (S.cdz[lo + j].x - di) : (S.cdz[lo + j + 1].x - di);
+                    const float db = (jb < i) ? (S.cdz[lo + jb].x - di) : (S.cdz[lo + jb + 1].x - di);
+                    prod *= (na * nb) / (da * db);
+                }
+                if (j < K - 1) {
+                    const float num = (S.cdz[S.org[lo + j]].x - di) + S.tq[lo + j];
                     const float den = (j < i) ? (S.cdz[lo + j].x - di) : (S.cdz[lo + j + 1].x - di);
                     prod *= num / den;
                 }
