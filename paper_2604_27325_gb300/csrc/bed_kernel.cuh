@@ -190,6 +190,15 @@ __host__ __device__ constexpr int a1_col_lanes()
     return 2;
 }
 
+// One-instruction square root (relative error about 2^-23) of a non-negative argument, subnormals
+// flushed to zero; used for the Householder norms and the Gu-Eisenstat z-hat.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Sort key with a total order: NaN sorts last, ties broken by index by the callers.
 __device__ __forceinline__ float sort_key(float x) { return isnan(x) ? INFINITY : x; }
 
@@ -607,6 +616,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 const float c = 0.5f * tau_prev * row_lane_sum<NTC>(dot);  // (tau/2) p.v of step k - 1
                 const float uk = Ur[k];
                 const float wk = fmaf(-c, uk, Pr[k]);
+                if (warp == wlast && lane == 0) S.d[k] = fmaf(-2.f * uk, wk, Yr[k]);
                 // w of step k - 1 (zero on finished rows) and x = column k of the updated matrix
                 float wr[TR], xr[TR];
                 float part = 0.f;
@@ -649,7 +659,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 const float alpha = fmaf(-fmaf(-c, u1, Pr[k + 1]), uk, fmaf(-u1, wk, Yr[k + 1]));
                 // reflector k; when x is already zero below its first entry, tau = 0 and beta = alpha.
                 // |beta| = nrm and |alpha - beta| >= nrm: both normal, far from overflow
-                const float nrm = sqrtf(fmaf(alpha, alpha, xn2));
+                const float nrm = sqrt_approx(fmaf(alpha, alpha, xn2));
                 const bool refl = xn2 > 0.f;
                 const float beta = refl ? ((alpha >= 0.f) ? -nrm : nrm) : alpha;
                 tau = refl ? (beta - alpha) * rcp_approx(beta) : 0.f;
@@ -666,7 +676,6 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
 #pragma unroll
                     for (int ii = 0; ii < TR; ++ii) S.A[yt_index<NMAX>(i0 + ii, k)] = vr[ii];
                     if (lane == 0) {
-                        S.d[k] = fmaf(-2.f * uk, wk, Yr[k]);
                         S.e[k] = beta;
                         S.tau[k] = tau;
                     }
@@ -964,7 +973,8 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 }
             }
             prod = gprod<G>(prod);
-            if (own && sub == 0) S.zh[lo + i] = copysignf(sqrtf(fmaxf(prod, 0.f)), S.cz[lo + i]);
+            // (a product below the normal range flushes to zero: |z-hat| < 1e-19 is a negligible coupling)
+            if (own && sub == 0) S.zh[lo + i] = copysignf(sqrt_approx(fmaxf(prod, 0.f)), S.cz[lo + i]);
         }
         team_sync<NT>(bar_id);
         // P7: eigenvectors of the merge (Eq. (24)) in sorted-pole rows, rotations undone
