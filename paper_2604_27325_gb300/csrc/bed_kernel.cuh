@@ -287,7 +287,7 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
             const float rz = rho * zn2;
             const float fro2 = fmaf(rz, rz, fmaf(2.f * rho, sdz, sd2));
             const float err2 = 4.f * (K + 4) * kU * fmaf(rz, rz, fmaf(2.f * rho, sdza, sd2));
-            const float fro = sqrtf(fmaxf(fro2 + err2, 0.f));
+            const float fro = sqrt_approx(fmaxf(fro2 + err2, 0.f));  // 2^-23: inside the 4u margin below
             const float dtop = dz[K - 1].x;
             const float uf = (fro - dtop) + 4.f * kU * (fro + fabsf(dtop));
             if (uf > 0.f && uf < U) U = uf;
@@ -827,7 +827,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                     int bex = 0;
                     if (bscale > 0.f) frexpf(bscale, &bex);
                     S.brho[lb] = rho;
-                    S.bnz[lb] = sqrtf(nz2);
+                    S.bnz[lb] = sqrt_approx(nz2);
                     S.btol[lb] = kp.defl_c * kU * bscale;
                     S.bsc[lb] = ldexpf(1.f, -bex);
                     S.brot[lb] = 0;
@@ -848,10 +848,11 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 int j = t + 1;
                 while (j < hi && rho * fabsf(S.zs[j]) * nz <= tol) ++j;
                 if (j < hi) {
+                    // c s = zp zj / (zp^2 + zj^2); the test is loosened by 2 so that no pair the exact
+                    // test of P3 (with hypot) would rotate is missed
                     const float zj = S.zs[j];
-                    const float r = hypotf(zp, zj);
-                    const float cc = zj / r, ss = zp / r;
-                    if (fabsf((S.ds[j] - S.ds[t]) * cc * ss) <= tol) {
+                    const float cs = zp * zj * rcp_approx(fmaf(zp, zp, zj * zj));
+                    if (fabsf((S.ds[j] - S.ds[t]) * cs) <= 2.f * tol) {
                         S.brot[lb] = 1;
                         S.flag_rot = 1;
                     }
@@ -964,7 +965,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                     const float nb = (S.cdz[S.org[lo + jb]].x - di) + S.tq[lo + jb];
                     const float da = (j < i) ? (S.cdz[lo + j].x - di) : (S.cdz[lo + j + 1].x - di);
                     const float db = (jb < i) ? (S.cdz[lo + jb].x - di) : (S.cdz[lo + jb + 1].x - di);
-                    prod *= (na * nb) / (da * db);
+                    prod *= (na * nb) * rcp_approx(da * db);
                 }
                 if (j < K - 1) {
                     const float num = (S.cdz[S.org[lo + j]].x - di) + S.tq[lo + j];
