@@ -84,6 +84,8 @@ def lib():
             L.orc_rank_one_eig.argtypes = [C.c_int, dp, dp, C.c_double, C.POINTER(Opts), dp, dp,
                                            C.POINTER(Stats)]
             L.orc_tridiag_eig.argtypes = [C.c_int, dp, dp, C.POINTER(Opts), dp, dp, C.POINTER(Stats)]
+            L.orc_tridiag_ql.argtypes = [C.c_int, dp, dp, dp, dp]
+            L.orc_tridiag_ql.restype = C.c_int
             L.orc_eigh.argtypes = [C.c_int, dp, C.POINTER(Opts), dp, dp, C.POINTER(Stats)]
             L.orc_eigh_batch_f32.argtypes = [C.c_int64, C.c_int, C.POINTER(C.c_float), C.POINTER(Opts),
                                              dp, dp, C.c_int, C.POINTER(Stats)]
@@ -135,6 +137,16 @@ def eig2(a, b, c):
     lam, Q = np.zeros(2), np.zeros(4)
     lib().orc_eig2(a, b, c, _dp(lam), _dp(Q))
     return lam, Q.reshape(2, 2)
+
+
+def tridiag_ql(d, e):
+    """a3 for larger leaves: implicit QL with Wilkinson shifts. Returns (lam ascending, Q, capped)."""
+    d, e = _f64(d), _f64(e)
+    s = d.shape[0]
+    e = np.concatenate([e, [0.0]])
+    lam, Q = np.zeros(s), np.zeros((s, s))
+    bad = lib().orc_tridiag_ql(s, _dp(d), _dp(e), _dp(lam), _dp(Q))
+    return lam, Q, bad
 
 
 def secular_eval(d, z, rho, o, tau):

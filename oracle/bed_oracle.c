@@ -14,7 +14,10 @@
  *       reduction (Golub & Van Loan, "Matrix Computations", Alg. 8.3.1).
  *   a2  Divide: rank-one tearing T = blkdiag(T1^, T2^) + |beta| v v^T,
  *       Eq. (1)-(3), recursively until the blocks are 2x2 (Sec. 2.1).
- *   a3  Leaves: one Givens/Jacobi rotation per 2x2 block (Sec. 2.2).
+ *   a3  Leaves: one Givens/Jacobi rotation per 2x2 block (Sec. 2.2); with a
+ *       larger leaf size, blocks of 3..8 rows by the implicit QL iteration with
+ *       Wilkinson shifts (the "batched QR" leaf option the paper mentions,
+ *       Sec. 2.2; Golub & Van Loan Sec. 8.3, written in the QL direction).
  *   a4  Conquer: block spectral form Eq. (4) and coupling vector z Eq. (5);
  *       deflation (the paper does not describe it; Dongarra-Sorensen reading).
  *   a5  Secular equation Eq. (8) under the interlacing constraint Eq. (9)-(12):
@@ -53,7 +56,8 @@ typedef struct {
     int max_halley_iters;   /* cap on Halley steps */
     double stop_c;          /* Halley stops when |f| <= c u (1 + rho sum |z^2/(d-lambda)|) */
     double deflate_c;       /* deflation tolerance = c u max(max|d|, rho |z|^2) */
-    int leaf_size;          /* divide until blocks have at most this many rows (1 or 2) */
+    int leaf_size;          /* divide until blocks have at most this many rows (1..8); blocks of 3
+                               or more rows are solved by the tridiagonal QL iteration */
 } orc_opts;
 
 typedef struct {
@@ -221,6 +225,91 @@ void orc_eig2(double a, double b, double c, double* lam, double* Q)
     Q[1] = sn;
     Q[2] = -sn;
     Q[3] = cs;
+}
+
+/*
+ * a3 (larger leaves): eigendecomposition of the s x s tridiagonal (d, e) by the
+ * implicit QL iteration with Wilkinson shifts. For the leading unreduced block
+ * [l, mm] (mm the first index with a negligible e[mm]) one step chases the
+ * bulge from the bottom: the shift is the eigenvalue of the top 2x2 block of
+ * [l, mm] nearer to d[l], and rotations in planes (i, i+1), i = mm-1 .. l,
+ * are accumulated into the columns of Q. Output as orc_tridiag_eig: lam
+ * ascending, Q row-major with eigenvectors as columns. Returns the number of
+ * eigenvalues that hit the iteration cap.
+ */
+int orc_tridiag_ql(int s, const double* d_in, const double* e_in, double* lam, double* Q)
+{
+    double d[ORC_NMAX], e[ORC_NMAX];
+    int bad = 0;
+    for (int i = 0; i < s; i++) {
+        d[i] = d_in[i];
+        e[i] = (i + 1 < s) ? e_in[i] : 0.0;
+        for (int j = 0; j < s; j++) Q[i * s + j] = (i == j) ? 1.0 : 0.0;
+    }
+    for (int l = 0; l < s; l++) {
+        int iter = 0;
+        for (;;) {
+            int mm = l;
+            while (mm < s - 1 && fabs(e[mm]) > ORC_U * (fabs(d[mm]) + fabs(d[mm + 1]))) mm++;
+            if (mm == l) break;
+            if (++iter > 60) {
+                bad++;
+                break;
+            }
+            /* shift: the eigenvalue of [[d_l, e_l], [e_l, d_l+1]] nearer to d_l is d_l - e_l/(g + sign(g) r)
+               with g = (d_l+1 - d_l)/(2 e_l), r = sqrt(g^2 + 1); the chase starts from d_mm minus it */
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[mm] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+            double sn = 1.0, cs = 1.0, p = 0.0;
+            int restarted = 0;
+            for (int i = mm - 1; i >= l; i--) {
+                double f = sn * e[i], b = cs * e[i];
+                r = hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) { /* the bulge vanished: the block splits at i + 1 */
+                    d[i + 1] -= p;
+                    e[mm] = 0.0;
+                    restarted = 1;
+                    break;
+                }
+                sn = f / r;
+                cs = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * sn + 2.0 * cs * b;
+                p = sn * r;
+                d[i + 1] = g + p;
+                g = cs * r - b;
+                for (int k = 0; k < s; k++) { /* columns i, i+1 of Q by the same rotation */
+                    double qa = Q[k * s + i], qb = Q[k * s + i + 1];
+                    Q[k * s + i + 1] = sn * qa + cs * qb;
+                    Q[k * s + i] = cs * qa - sn * qb;
+                }
+            }
+            if (restarted) continue;
+            d[l] -= p;
+            e[l] = g;
+            e[mm] = 0.0;
+        }
+    }
+    /* ascending order (selection sort, columns of Q follow) */
+    for (int i = 0; i < s; i++) {
+        int m = i;
+        for (int j = i + 1; j < s; j++)
+            if (d[j] < d[m]) m = j;
+        if (m != i) {
+            double t = d[i];
+            d[i] = d[m];
+            d[m] = t;
+            for (int k = 0; k < s; k++) {
+                t = Q[k * s + i];
+                Q[k * s + i] = Q[k * s + m];
+                Q[k * s + m] = t;
+            }
+        }
+    }
+    memcpy(lam, d, sizeof(double) * s);
+    return bad;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -573,6 +662,11 @@ void orc_tridiag_eig(int s, const double* d, const double* e, const orc_opts* op
     if (s == 1) {
         lam[0] = d[0];
         Q[0] = 1.0;
+        return;
+    }
+    if (s >= 3 && s <= op->leaf_size) {
+        int bad = orc_tridiag_ql(s, d, e, lam, Q);
+        if (st) st->not_conv += bad;
         return;
     }
     if (s == 2 && op->leaf_size >= 2) {

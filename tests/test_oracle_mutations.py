@@ -44,6 +44,8 @@ MUTATIONS = {
     "backward_gap_sign": ("m = vg / (W[j] - W[i]);", "m = vg / (W[i] - W[j]);"),
     "backward_not_symmetrized": ("gA[i * n + j] = 0.5 * (G[i * n + j] + G[j * n + i]);", "gA[i * n + j] = G[i * n + j];"),
     "deflation_drops_rho": ("defl[p] = (rho * fabs(zz[p]) * nz <= tol);", "defl[p] = (fabs(zz[p]) <= 0.5);"),
+    "ql_rotation_sign": ("Q[k * s + i + 1] = sn * qa + cs * qb;", "Q[k * s + i + 1] = -sn * qa + cs * qb;"),
+    "ql_bulge_term": ("r = (d[i] - g) * sn + 2.0 * cs * b;", "r = (d[i] - g) * sn + cs * b;"),
 }
 
 

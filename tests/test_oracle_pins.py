@@ -336,14 +336,73 @@ def test_tridiagonal_toeplitz_closed_form(n):
         assert min(np.linalg.norm(Q[:, col] - v), np.linalg.norm(Q[:, col] + v)) < 1e-12 * n
 
 
-@pytest.mark.parametrize("leaf", [1, 2])
+@pytest.mark.parametrize("leaf", [1, 2, 3, 4, 5, 8])
 def test_tridiag_eig_leaf_size(leaf):
-    """Sec. 2.2: dividing down to 1x1 or 2x2 blocks gives the same eigendecomposition."""
+    """Sec. 2.2: dividing down to blocks of 1..8 rows (QL leaves from 3 rows) gives the same
+    eigendecomposition."""
     rng = np.random.default_rng(12)
-    n = 21
-    d, e = rng.standard_normal(n), rng.standard_normal(n - 1)
-    lam, Q, _ = oracle.tridiag_eig(d, e, oracle.default_opts(leaf_size=leaf))
-    _check_eigpairs(_tri(d, e), lam, Q, 1e-13 * n)
+    for n in (21, 37, 64):
+        d, e = rng.standard_normal(n), rng.standard_normal(n - 1)
+        lam, Q, st = oracle.tridiag_eig(d, e, oracle.default_opts(leaf_size=leaf))
+        _check_eigpairs(_tri(d, e), lam, Q, 1e-13 * n)
+        assert st.not_conv == 0
+
+
+# ----------------------------------------------------------------------------- a3: QL leaves
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_tridiag_ql_against_lapack(s):
+    """Implicit QL leaf: eigenpairs of random tridiagonals against LAPACK, orthogonality, ascending."""
+    rng = np.random.default_rng(100 + s)
+    for trial in range(20):
+        d = rng.standard_normal(s) * (10.0 ** rng.integers(-3, 4))
+        e = rng.standard_normal(max(s - 1, 0)) * (10.0 ** rng.integers(-3, 4))
+        lam, Q, bad = oracle.tridiag_ql(d, e)
+        assert bad == 0
+        T = _tri(d, e)
+        nrm = max(np.abs(np.linalg.eigvalsh(T)).max(), 1e-300)
+        assert np.all(np.diff(lam) >= 0)
+        assert np.allclose(lam, np.linalg.eigvalsh(T), rtol=0, atol=1e-14 * nrm * s)
+        assert np.linalg.norm(Q.T @ Q - np.eye(s)) < 1e-14 * s
+        assert np.linalg.norm(T @ Q - Q * lam[None, :]) < 1e-14 * nrm * s
+
+
+def test_tridiag_ql_special_cases():
+    """Split tridiagonals (zero couplings), repeated eigenvalues and the Toeplitz closed form."""
+    # zero off-diagonals: diagonal entries are the eigenvalues, Q a permutation
+    d = np.array([3.0, -1.0, 2.0, 0.5, 2.0])
+    lam, Q, bad = oracle.tridiag_ql(d, np.zeros(4))
+    assert bad == 0 and np.array_equal(lam, np.sort(d))
+    assert np.allclose(np.abs(Q) @ np.ones(5), np.ones(5))
+    # one interior zero coupling: two independent blocks
+    d, e = np.array([1.0, 2.0, 3.0, 4.0, 5.0, 6.0]), np.array([0.5, 0.25, 0.0, 0.75, 1.0])
+    lam, Q, bad = oracle.tridiag_ql(d, e)
+    assert bad == 0
+    _check_eigpairs(_tri(d, e), lam, Q, 1e-14 * 6 * 6)
+    # Toeplitz: eigenvalues a + 2b cos(k pi/(s+1)), a double root free family
+    for s in (3, 5, 8):
+        a, b = 0.3, -0.7
+        lam, Q, bad = oracle.tridiag_ql(np.full(s, a), np.full(s - 1, b))
+        ref = np.sort(a + 2 * b * np.cos(np.arange(1, s + 1) * np.pi / (s + 1)))
+        assert bad == 0 and np.allclose(lam, ref, rtol=0, atol=1e-14 * s)
+    # a matrix with a repeated eigenvalue (glued identical blocks with zero coupling)
+    d, e = np.array([2.0, 1.0, 2.0, 1.0]), np.array([0.5, 0.0, 0.5])
+    lam, Q, bad = oracle.tridiag_ql(d, e)
+    assert bad == 0
+    _check_eigpairs(_tri(d, e), lam, Q, 1e-14 * 16)
+
+
+@pytest.mark.parametrize("leaf", [4, 8])
+def test_eigh_with_ql_leaves(leaf):
+    """The whole path with QL leaves against LAPACK on covariances and gapped spectra."""
+    from paper_2604_27325_gb300 import workloads as wl
+    for n in (9, 16, 40, 64):
+        A = wl.covariance(2, n, seed=70 + n).astype(np.float64)
+        for b in range(2):
+            W, V, st = oracle.eigh(A[b], oracle.default_opts(leaf_size=leaf))
+            assert st.not_conv == 0
+            _check_eigpairs(A[b], W, V, 1e-12 * n)
 
 
 # ----------------------------------------------------------------------------- a1-a9: whole path
