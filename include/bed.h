@@ -59,7 +59,8 @@ enum {
  * defaults below. Passing NULL wherever a `const bed_params*` is taken means the defaults.
  */
 typedef struct {
-    int leaf_size;           /* divide (Sec. 2.1) until blocks have <= leaf_size rows: 1 or 2 (default 2) */
+    int leaf_size;           /* divide (Sec. 2.1) until blocks have <= leaf_size rows, 1..8 (default 8);
+                                blocks of 3..8 rows are solved by the implicit QL iteration (Sec. 2.2) */
     int k_multisection;      /* k of Eq. (16), >= 2 (default 4) */
     int max_section_iters;   /* cap on multi-section steps per root, 0..256 (default 24) */
     int max_halley_iters;    /* cap on Halley steps per root, 1..256 (default 32) */
@@ -122,10 +123,10 @@ bed_status bed_eigh_f32_counted(const float* A, float* W, float* V, int32_t* inf
  */
 typedef struct {
     unsigned char team[65]; /* team type for each n */
-    unsigned char leaf[65]; /* leaf size (1 or 2) for each n */
+    unsigned char leaf[65]; /* leaf size (1..8) for each n */
 } bed_ragged_tuning;
 
-/* Fills *t with the built-in choice: type 2 for n <= 16, type 1 for n <= 32, type 0 above; leaf 2. */
+/* Fills *t with the built-in choice: type 2 for n <= 16, type 1 for n <= 32, type 0 above; leaf 8. */
 void bed_ragged_default_tuning(bed_ragged_tuning* t);
 
 /* Bytes of device workspace bed_eigh_ragged_f32 needs for `count` matrices (a multiple of 256). */

@@ -1,8 +1,8 @@
 """Autotuner for ragged launches: picks, for every n, the team shape and leaf size by measurement.
 
 For each n the candidates are the team types whose size class holds n (one 256-thread team, two
-128-thread, four 64-thread or eight 32-thread teams per block) times the two leaf sizes of the divide
-tree (Sec. 2.1-2.2: 1x1 or 2x2 leaves). Each candidate solves a uniform batch of seeded covariance
+128-thread, four 64-thread or eight 32-thread teams per block) times three leaf sizes of the divide
+tree (Sec. 2.1-2.2: 2x2 leaves, or QL leaves of up to 4 or 8 rows). Each candidate solves a uniform batch of seeded covariance
 matrices of that n through the ragged entry point; the fastest per-matrix time wins. Results are kept
 as JSON keyed by the GPU's name, and :func:`load` turns them into a ``bed_ragged_tuning``.
 """
@@ -52,7 +52,7 @@ def tune(ns=range(1, 65), batch: int = 2048, reps: int = 10, path: str | None = 
         for team, cap in TEAM_CAP.items():
             if n > cap:
                 continue
-            for leaf in (1, 2):
+            for leaf in (2, 4, 8):
                 t = B.bed_ragged_default_tuning()
                 t.team[n], t.leaf[n] = team, leaf
                 rb = B.RaggedBatch([n] * batch, tuning=t).load(list(A))
@@ -83,7 +83,7 @@ def load(path: str | None = None) -> B.bed_ragged_tuning:
         return t
     for k, v in table.items():
         n = int(k)
-        if 1 <= n <= 64 and n <= TEAM_CAP.get(int(v["team"]), 0) and int(v["leaf"]) in (1, 2):
+        if 1 <= n <= 64 and n <= TEAM_CAP.get(int(v["team"]), 0) and 1 <= int(v["leaf"]) <= 8:
             t.team[n], t.leaf[n] = int(v["team"]), int(v["leaf"])
     return t
 

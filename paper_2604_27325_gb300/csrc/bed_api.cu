@@ -44,7 +44,7 @@ bed_status cuda_fail(cudaError_t e)
 
 bool build_plan(int n, int leaf_size, Plan* P)
 {
-    if (n < 1 || n > kMaxN || (leaf_size != 1 && leaf_size != 2)) return false;
+    if (n < 1 || n > kMaxN || leaf_size < 1 || leaf_size > kMaxLeaf) return false;
     std::vector<MergeRec> merges;
     std::vector<int> leaves;
     split(0, n, 0, leaf_size, merges, leaves);
@@ -105,7 +105,7 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
 {
     bed_default_params(prm);
     if (p) *prm = *p;
-    if (prm->leaf_size != 1 && prm->leaf_size != 2) return false;
+    if (prm->leaf_size < 1 || prm->leaf_size > kMaxLeaf) return false;
     if (prm->k_multisection < 2 || prm->k_multisection > 64) return false;
     if (prm->max_section_iters < 0 || prm->max_section_iters > 256) return false;
     if (prm->max_halley_iters < 1 || prm->max_halley_iters > 256) return false;
@@ -168,7 +168,7 @@ bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_
 bool tuning_valid(const bed_ragged_tuning& t)
 {
     for (int n = 1; n <= kMaxN; ++n) {
-        if (t.leaf[n] != 1 && t.leaf[n] != 2) return false;
+        if (t.leaf[n] < 1 || t.leaf[n] > kMaxLeaf) return false;
         const int tt = t.team[n];
         if (tt > 3) return false;
         const int cap = tt == 0 ? 64 : (tt == 1 ? 32 : 16);
@@ -189,7 +189,7 @@ void bed_ragged_default_tuning(bed_ragged_tuning* t)
     std::memset(t, 0, sizeof *t);
     for (int n = 0; n <= bed::kMaxN; ++n) {
         t->team[n] = static_cast<unsigned char>(n <= 16 ? 2 : (n <= 32 ? 1 : 0));
-        t->leaf[n] = 2;
+        t->leaf[n] = 8;
     }
 }
 
@@ -228,7 +228,7 @@ bed_status bed_eigh_ragged_f32(const float* A, const int64_t* offsets, const int
 void bed_default_params(bed_params* p)
 {
     if (!p) return;
-    p->leaf_size = 2;
+    p->leaf_size = 8;
     p->k_multisection = 4;
     p->max_section_iters = 24;
     p->max_halley_iters = 32;

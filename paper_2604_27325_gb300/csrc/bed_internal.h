@@ -10,6 +10,7 @@
 namespace bed {
 
 constexpr int kMaxN = 64;
+constexpr int kMaxLeaf = 8;  // largest leaf of the divide tree (3..8 rows: implicit QL leaf solver)
 constexpr int kMaxLevels = 8;  // merge levels of a tree over n <= 64 rows (6 with 1x1 leaves)
 
 // The divide tree of Sec. 2.1 for one n: blocks are split at floor(s/2) until they have at most
@@ -21,7 +22,7 @@ struct Plan {
     int nmerge;
     int nlevels;                            // merge levels; level 0 is the deepest
     unsigned long long cut_mask;            // bit t: the tridiagonal is torn between rows t and t+1
-    uint8_t leaf_lo[kMaxN], leaf_hi[kMaxN]; // leaves [lo, hi), 1 or 2 rows
+    uint8_t leaf_lo[kMaxN], leaf_hi[kMaxN]; // leaves [lo, hi), 1 to kMaxLeaf rows
     uint8_t m_lo[kMaxN], m_mid[kMaxN], m_hi[kMaxN];  // merges, grouped by level (deepest first)
     uint8_t level_start[kMaxLevels + 1];    // merges of level L: [level_start[L], level_start[L+1])
     uint8_t blk[kMaxLevels][kMaxN];         // merge that owns row/column t at level L, 0xFF if none

@@ -245,6 +245,109 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 }
 
 // ---------------------------------------------------------------------------------------------
+// a3 for leaves of 3..8 rows: implicit QL iteration with Wilkinson shifts (the small-block solver the
+// paper offers in place of dividing down to 2x2 blocks, Sec. 2.2). Every lane of a group of 8 runs
+// the same scalar recurrence on its own register copy of (d, e) -- no communication -- and applies
+// each plane rotation to its own row r of the leaf's eigenvector block. The loops are unrolled over
+// the 8 possible positions and predicated on the runtime bounds, so d, e and z stay in registers.
+// Writes the eigenvalues (lane 0) and row r of the eigenvectors; returns false if an eigenvalue hit
+// the iteration cap.
+// ---------------------------------------------------------------------------------------------
+// c ? a : b through an explicit predicate select: written this way so that a chain of them over an
+// unrolled register array is not turned back into an indexed (local-memory) load
+__device__ __forceinline__ float selp(bool c, float a, float b)
+{
+    float r;
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %3, 0;\n\tselp.f32 %0, %1, %2, p;\n\t}"
+        : "=f"(r)
+        : "f"(a), "f"(b), "r"(static_cast<int>(c)));
+    return r;
+}
+
+constexpr int kLeafMax = 8;
+
+__device__ __forceinline__ bool ql_leaf(const float* __restrict__ dg, const float* __restrict__ eg, int m,
+                                        int r, float* __restrict__ lam_out, float* __restrict__ q_row)
+{
+    float d[kLeafMax], e[kLeafMax], z[kLeafMax];
+#pragma unroll
+    for (int j = 0; j < kLeafMax; ++j) {
+        d[j] = (j < m) ? dg[j] : 0.f;
+        e[j] = (j < m - 1) ? eg[j] : 0.f;
+        z[j] = (j == r) ? 1.f : 0.f;
+    }
+    bool ok = true;
+    for (int l = 0; l < m; ++l) {
+        for (int iter = 0;; ++iter) {
+            // the first negligible coupling at or after l bounds the unreduced block [l, mm]
+            int mm = m - 1;
+#pragma unroll
+            for (int j = kLeafMax - 2; j >= 0; --j)
+                if (j >= l && j < m - 1 && fabsf(e[j]) <= 0x1p-23f * (fabsf(d[j]) + fabsf(d[j + 1]))) mm = j;
+            if (mm == l) break;
+            if (iter >= 30) {
+                ok = false;
+                break;
+            }
+            float dl = 0.f, dl1 = 0.f, el = 0.f, dmm = 0.f;
+#pragma unroll
+            for (int j = 0; j < kLeafMax; ++j) {
+                dl = selp(j == l, d[j], dl);
+                el = selp(j == l, e[j], el);
+                dl1 = selp(j == l + 1, d[j], dl1);
+                dmm = selp(j == mm, d[j], dmm);
+            }
+            // Wilkinson shift: the eigenvalue of the top 2x2 block nearer to d_l; the chase starts from
+            // d_mm minus it
+            float g = (dl1 - dl) * rcp_approx(2.f * el);
+            const float rr = sqrt_approx(fmaf(g, g, 1.f));
+            g = dmm - dl + el * rcp_approx(g + copysignf(rr, g));
+            float sn = 1.f, cs = 1.f, p = 0.f;
+            bool split = false;  // the bulge vanished: the block splits, the step ends early
+#pragma unroll
+            for (int i = kLeafMax - 2; i >= 0; --i) {
+                if (i < mm && i >= l && !split) {
+                    const float f = sn * e[i], b = cs * e[i];
+                    const float h = sqrt_approx(fmaf(f, f, g * g));
+                    e[i + 1] = h;
+                    if (h == 0.f) {
+                        d[i + 1] -= p;
+                        split = true;
+                    } else {
+                        const float ih = rcp_approx(h);
+                        sn = f * ih;
+                        cs = g * ih;
+                        g = d[i + 1] - p;
+                        const float t = fmaf(d[i] - g, sn, 2.f * cs * b);
+                        p = sn * t;
+                        d[i + 1] = g + p;
+                        g = fmaf(cs, t, -b);
+                        const float za = z[i], zb = z[i + 1];
+                        z[i + 1] = fmaf(sn, za, cs * zb);
+                        z[i] = fmaf(cs, za, -sn * zb);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kLeafMax; ++j) {
+                if (j == l && !split) {
+                    d[j] -= p;
+                    e[j] = g;
+                }
+                if (j == mm) e[j] = 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kLeafMax; ++j)
+        if (j < m) {
+            if (r == 0) lam_out[j] = d[j];
+            if (r < m) q_row[j] = z[j];
+        }
+    return ok;
+}
+
+// ---------------------------------------------------------------------------------------------
 // a5: one secular root (Eq. (8)) of the compacted, ascending, unit-scaled poles
 // d[0] < ... < d[K-1] with couplings z_j^2, stored as pairs dz[j] = (d[j], z_j^2). Root q lies in (d_q, d_{q+1}) for q < K-1
 // (Eq. (9)) and in (d_{K-1}, upper] for q = K-1 (Eq. (10)-(11)). Called by EVERY lane of the warp (non-participating lanes pass
@@ -756,7 +859,15 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
     team_sync<NT>(bar_id);
 
     // ---------------- a3: leaves ------------------------------------------------------------
-    if (tid < plan.nleaves) {
+    for (int lf = tid >> 3; lf < plan.nleaves; lf += NT >> 3) {
+        const int lo = plan.leaf_lo[lf], m = plan.leaf_hi[lf] - lo;
+        if (m >= 3) {
+            const int r = tid & 7;
+            const bool ok = ql_leaf(&S.d[lo], &S.e[lo], m, r, &S.lam[lo], &S.Q[(lo + min(r, m - 1)) * LD + lo]);
+            if (!ok && r == 0) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
+        }
+    }
+    if (tid < plan.nleaves && plan.leaf_hi[tid] - plan.leaf_lo[tid] <= 2) {
         const int lo = plan.leaf_lo[tid];
         if (plan.leaf_hi[tid] - lo == 1) {
             S.lam[lo] = S.d[lo];

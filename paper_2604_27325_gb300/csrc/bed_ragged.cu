@@ -34,8 +34,8 @@ __host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a
 constexpr size_t kRaggedSmem = cmax(cmax(slice_bytes<64, 4>(), 2 * slice_bytes<32, 4>()),
                                     cmax(4 * slice_bytes<16, 4>(), 8 * slice_bytes<16, 2>()));
 
-// Divide trees for every n and both leaf sizes, written once per device (setup before first use).
-__device__ Plan g_plans[2][kMaxN + 1];
+// Divide trees for every n and every leaf size, written once per device (setup before first use).
+__device__ Plan g_plans[kMaxLeaf][kMaxN + 1];
 
 struct RaggedHeader {
     unsigned int next_unit;                   // work counter (reset by the pre-kernel)
@@ -186,9 +186,9 @@ cudaError_t ragged_setup(int* grid)
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_setup_done[dev]) {
-        static Plan host_plans[2][kMaxN + 1];
+        static Plan host_plans[kMaxLeaf][kMaxN + 1];
         std::memset(host_plans, 0, sizeof host_plans);
-        for (int leaf = 1; leaf <= 2; ++leaf)
+        for (int leaf = 1; leaf <= kMaxLeaf; ++leaf)
             for (int n = 1; n <= kMaxN; ++n) build_plan(n, leaf, &host_plans[leaf - 1][n]);
         e = cudaMemcpyToSymbol(g_plans, host_plans, sizeof host_plans);
         if (e != cudaSuccess) return e;

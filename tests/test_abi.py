@@ -36,7 +36,7 @@ def test_constants_and_strings():
     assert B.bed_status_string(99) == "BED_UNKNOWN_STATUS"
     assert C.sizeof(B.bed_counters) == 32
     p = B.bed_default_params()
-    assert (p.leaf_size, p.k_multisection, p.retire_by_vote, p.threads_per_matrix) == (2, 4, 1, 0)
+    assert (p.leaf_size, p.k_multisection, p.retire_by_vote, p.threads_per_matrix) == (8, 4, 1, 0)
     assert p.section_rel_eps == 2.0**-1
 
 
@@ -65,7 +65,7 @@ def test_empty_batch_is_ok_without_launch():
 
 @pytest.mark.parametrize(
     "field,value",
-    [("leaf_size", 3), ("leaf_size", 0), ("k_multisection", 1), ("max_halley_iters", 0),
+    [("leaf_size", 9), ("leaf_size", 0), ("k_multisection", 1), ("max_halley_iters", 0),
      ("max_section_iters", -1), ("section_rel_eps", 0.0), ("section_rel_eps", 1.0), ("stop_c", 0.5),
      ("deflation_tol_scale", 0.0), ("retire_by_vote", 2), ("threads_per_matrix", 100)],
 )
@@ -74,7 +74,7 @@ def test_bad_params(field, value):
     assert B.bed_eigh_f32(FAKE, FAKE, FAKE + 4096, None, 3, 8, p) == B.BED_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("leaf", [1, 2])
+@pytest.mark.parametrize("leaf", [1, 2, 3, 5, 8])
 def test_divide_tree_plan(leaf):
     """Sec. 2.1 divide tree: split at floor(s/2) down to <= leaf rows; children merge before parents."""
     for n in range(1, 65):
@@ -102,7 +102,9 @@ def test_divide_tree_plan(leaf):
     with pytest.raises(ValueError):
         B.bed_plan_describe(65)
     with pytest.raises(ValueError):
-        B.bed_plan_describe(8, 3)
+        B.bed_plan_describe(8, 9)
+    with pytest.raises(ValueError):
+        B.bed_plan_describe(8, 0)
 
 
 def test_no_cpu_fallback():
@@ -132,5 +134,5 @@ def test_ragged_validation_before_launch():
     t.team[20] = 2  # a 64-thread team (n <= 16) cannot hold n = 20
     assert B.bed_eigh_ragged_f32(**{**args, "tuning": t}) == B.BED_ERR_INVALID_ARG
     t = B.bed_ragged_default_tuning()
-    t.leaf[5] = 3
+    t.leaf[5] = 9
     assert B.bed_eigh_ragged_f32(**{**args, "tuning": t}) == B.BED_ERR_INVALID_ARG

@@ -160,7 +160,7 @@ def test_counters():
     matrices, roots, evals, deflated = cnt.tolist()
     assert matrices == 16
     # each merge of size s yields s eigenpairs: roots + deflated = sum of merge sizes
-    total = 16 * sum(hi - lo for lo, _, hi, _ in B.bed_plan_describe(32))
+    total = 16 * sum(hi - lo for lo, _, hi, _ in B.bed_plan_describe(32, B.make_params().leaf_size))
     assert roots + deflated == total
     assert roots > 0 and evals > roots
 
@@ -219,3 +219,35 @@ def test_many_batches_on_streams_match_single_calls(where):
         assert W.is_cuda == (where == "device")
         assert torch.equal(W.cpu(), W1.cpu()) and torch.equal(V.cpu(), V1.cpu())
         assert int((info != 0).sum()) == 0
+
+
+# ----------------------------------------------------------------------------- QL leaves (Sec. 2.2)
+
+
+@pytest.mark.parametrize("leaf", [3, 4, 5, 8])
+def test_every_n_with_ql_leaves(leaf):
+    """Leaves of up to `leaf` rows solved by the in-kernel implicit QL iteration, every n."""
+    p = B.make_params(leaf_size=leaf)
+    for n in range(1, 65):
+        A = np.concatenate([wl.covariance(3, n, seed=9200 + n), wl.known_spectrum(3, n, seed=9300 + n)[0]])
+        W, V, info = run_gpu(A, p)
+        Wo, Vo = run_oracle(A)
+        assert_parity(A, W, V, info, Wo, Vo, f"leaf={leaf} n={n}")
+
+
+@pytest.mark.parametrize("leaf", [4, 8])
+@pytest.mark.parametrize("name", ["zero", "identity", "diagonal", "repeated", "rank_one", "block_diagonal", "toeplitz"])
+def test_degenerate_inputs_with_ql_leaves(leaf, name):
+    for n in (3, 5, 8, 9, 16, 37, 64):
+        A = wl.special_cases(n)[name][None].repeat(2, axis=0)
+        W, V, info = run_gpu(A, B.make_params(leaf_size=leaf))
+        Wo, Vo = run_oracle(A)
+        assert_parity(A, W, V, info, Wo, Vo, f"{name} leaf={leaf} n={n}")
+
+
+@pytest.mark.parametrize("n", [16, 32, 48, 64])
+def test_uniform_covariance_with_ql_leaves(n):
+    A = wl.covariance(512, n)
+    W, V, info = run_gpu(A, B.make_params(leaf_size=8))
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W, V, info, Wo, Vo, f"covariance 512 x {n}, leaf 8")

@@ -42,7 +42,7 @@ def test_ragged_mixed_sizes_against_oracle():
 
 
 @pytest.mark.parametrize("team,n", [(0, 64), (0, 41), (0, 33), (1, 32), (1, 19), (2, 16), (2, 5), (3, 16), (3, 3)])
-@pytest.mark.parametrize("leaf", [1, 2])
+@pytest.mark.parametrize("leaf", [1, 2, 8])
 def test_ragged_equals_uniform_path_bitwise(team, n, leaf):
     """A ragged team runs the same per-matrix code as the uniform launch of the same shape."""
     A = wl.covariance(37, n, seed=500 + n)
