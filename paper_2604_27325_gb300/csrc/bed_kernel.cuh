@@ -720,16 +720,18 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 const float uk = Ur[k];
                 const float wk = fmaf(-c, uk, Pr[k]);
                 if (warp == wlast && lane == 0) S.d[k] = fmaf(-2.f * uk, wk, Yr[k]);
-                // w of step k - 1 (zero on finished rows) and x = column k of the updated matrix
+                // w of step k - 1 and x = column k of the updated matrix. v_{k-1} is zero on the
+                // finished rows i < k, so the update below leaves the active block exact without
+                // masking; the finished rows and columns pick up bounded values that no later step
+                // reads (the column sums and x are taken against v_k, zero there). Rows >= n stay zero.
                 float wr[TR], xr[TR];
                 float part = 0.f;
 #pragma unroll
                 for (int ii = 0; ii < TR; ++ii) {
                     const int i = i0 + ii;
-                    const float w = fmaf(-c, ur[ii], pr[ii]);
-                    wr[ii] = (i >= k) ? w : 0.f;
-                    xr[ii] = fmaf(-w, uk, fmaf(-ur[ii], wk, yr[ii]));
-                    if (i > k + 1 && i < n) part = fmaf(xr[ii], xr[ii], part);
+                    wr[ii] = fmaf(-c, ur[ii], pr[ii]);
+                    xr[ii] = fmaf(-wr[ii], uk, fmaf(-ur[ii], wk, yr[ii]));
+                    if (i > k + 1) part = fmaf(xr[ii], xr[ii], part);
                 }
                 // the update of step k - 1 needs only c: apply it to the tile (rows and columns >= k)
                 // while the reduction for reflector k is in flight
@@ -738,9 +740,8 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 load_vec<TC>(Ur + j0, uc);
 #pragma unroll
                 for (int jj = 0; jj < TC; ++jj) {
-                    const int j = j0 + jj;
                     const float u = uc[jj];
-                    const float w = (j >= k) ? fmaf(-c, u, pc[jj]) : 0.f;
+                    const float w = fmaf(-c, u, pc[jj]);
 #pragma unroll
                     for (int ii = 0; ii < TR; ++ii) a[ii][jj] = fmaf(-ur[ii], w, fmaf(-wr[ii], u, a[ii][jj]));
                 }
