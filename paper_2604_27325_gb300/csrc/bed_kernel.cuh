@@ -308,13 +308,15 @@ __device__ __forceinline__ bool ql_leaf(const float* __restrict__ dg, const floa
             for (int i = kLeafMax - 2; i >= 0; --i) {
                 if (i < mm && i >= l && !split) {
                     const float f = sn * e[i], b = cs * e[i];
-                    const float h = sqrt_approx(fmaf(f, f, g * g));
+                    const float h2 = fmaf(f, f, g * g);
+                    const float ih = rsqrtf(h2);  // one reciprocal square root gives h and 1/h
+                    const float h = h2 * ih;
                     e[i + 1] = h;
-                    if (h == 0.f) {
+                    if (h2 < FLT_MIN) {  // (a subnormal square flushes too: the bulge has vanished)
+                        e[i + 1] = 0.f;
                         d[i + 1] -= p;
                         split = true;
                     } else {
-                        const float ih = rcp_approx(h);
                         sn = f * ih;
                         cs = g * ih;
                         g = d[i + 1] - p;
@@ -1214,35 +1216,74 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             float* T = Tm + g * kBT * kBT;
             for (int e = lane; e < kBT * kBT; e += 32) T[e] = 0.f;
             __syncwarp();
-            // Gram entries Y[:, r]^T Y[:, j] for r < j, one pair per lane, stored at T[j][r]
-            int p = lane, r = 0;
-            while (r < kBT - 1 && p >= kBT - 1 - r) {
-                p -= kBT - 1 - r;
-                ++r;
-            }
-            const int j = r + 1 + p;
-            if (r < kBT - 1 && j < bsz) {
-                const int kr = k0 + r, kj = k0 + j;
-                float sg = 0.f;
-                for (int i = kj + 1; i < n; ++i)
-                    sg = fmaf(Yt[yt_index<NMAX>(i, kr)], Yt[yt_index<NMAX>(i, kj)], sg);
-                T[j * kBT + r] = sg;
+            // Gram entries Y[:, r]^T Y[:, j], r < j (28 pairs, r-major): every lane forms the products
+            // of its rows (two 16-byte reads per row), then a halving exchange over the 32 lanes
+            // leaves pair `lane` summed on lane `lane`; stored at T[j][r]
+            {
+                float v[32];
+#pragma unroll
+                for (int t = 0; t < 32; ++t) v[t] = 0.f;
+#pragma unroll
+                for (int m = 0; m < (NMAX + 31) / 32; ++m) {
+                    const int i = lane + 32 * m;
+                    if (i < NMAX) {
+                        const float4 ya = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0));
+                        const float4 yb = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0 + 4));
+                        const float y[kBT] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+                        int pp = 0;
+#pragma unroll
+                        for (int r = 0; r < kBT - 1; ++r)
+#pragma unroll
+                            for (int j = r + 1; j < kBT; ++j) {
+                                v[pp] = fmaf(y[r], y[j], v[pp]);
+                                ++pp;
+                            }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    const bool up = (lane & o) != 0;
+#pragma unroll
+                    for (int t = 0; t < o; ++t) {
+                        const float send = up ? v[t] : v[t + o];
+                        const float keep = up ? v[t + o] : v[t];
+                        v[t] = keep + __shfl_xor_sync(kFull, send, o);
+                    }
+                }
+                int p = lane, r = 0;
+                while (r < kBT - 1 && p >= kBT - 1 - r) {
+                    p -= kBT - 1 - r;
+                    ++r;
+                }
+                const int j = r + 1 + p;
+                if (r < kBT - 1 && j < bsz) T[j * kBT + r] = v[0];
             }
             __syncwarp();
-            // T[jj][jj] = tau_jj; T[0:jj, jj] = T[0:jj, 0:jj] w with w_s = -tau_jj Gram[s][jj]
-            for (int jj = 0; jj < bsz; ++jj) {
-                const float tj = S.tau[k0 + jj];
-                const float w = (lane < jj) ? -tj * T[jj * kBT + lane] : 0.f;
-                float acc = 0.f;
-                for (int s2 = 0; s2 < jj; ++s2) {
-                    const float ws = __shfl_sync(kFull, w, s2);
-                    if (lane <= s2) acc = fmaf(T[lane * kBT + s2], ws, acc);
+            // T[jj][jj] = tau_jj; T[0:jj, jj] = -tau_jj T[0:jj, 0:jj] Gram[0:jj, jj]: lane r keeps row r
+            // of T in registers and reads only its own earlier entries and the Gram column
+            {
+                float trow[kBT];
+#pragma unroll
+                for (int t = 0; t < kBT; ++t) trow[t] = 0.f;
+                for (int jj = 0; jj < bsz; ++jj) {
+                    const float tj = S.tau[k0 + jj];
+                    float acc = 0.f;
+#pragma unroll
+                    for (int s2 = 0; s2 < kBT; ++s2)
+                        if (s2 < jj) acc = fmaf(trow[s2], T[jj * kBT + s2], acc);
+                    const float val = (lane < jj) ? -tj * acc : ((lane == jj) ? tj : 0.f);
+#pragma unroll
+                    for (int s2 = 0; s2 < kBT; ++s2)
+                        if (s2 == jj) trow[s2] = val;
                 }
                 __syncwarp();
-                if (lane < jj) T[lane * kBT + jj] = acc;
-                if (lane == jj) T[jj * kBT + jj] = tj;
-                __syncwarp();
+                if (lane < kBT) {
+#pragma unroll
+                    for (int s2 = 0; s2 < kBT; ++s2)
+                        if (s2 >= lane) T[lane * kBT + s2] = trow[s2];
+                }
             }
+            __syncwarp();
             for (int e = lane; e < kBT * kBT; e += 32)
                 if (e % kBT < e / kBT) T[e] = 0.f;
         }
