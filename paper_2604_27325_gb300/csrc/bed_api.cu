@@ -2,6 +2,7 @@
 #include <cfloat>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -77,6 +78,20 @@ bool build_plan(int n, int leaf_size, Plan* P)
     }
     P->level_start[P->nlevels] = static_cast<uint8_t>(idx);
     return true;
+}
+
+// Divide trees of every n and leaf size, built once on first use (host memory, read-only afterwards).
+const Plan* cached_plan(int n, int leaf_size)
+{
+    static Plan plans[kMaxLeaf][kMaxN + 1];
+    static bool ok[kMaxLeaf][kMaxN + 1];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (int leaf = 1; leaf <= kMaxLeaf; ++leaf)
+            for (int m = 1; m <= kMaxN; ++m) ok[leaf - 1][m] = build_plan(m, leaf, &plans[leaf - 1][m]);
+    });
+    if (n < 1 || n > kMaxN || leaf_size < 1 || leaf_size > kMaxLeaf || !ok[leaf_size - 1][n]) return nullptr;
+    return &plans[leaf_size - 1][n];
 }
 
 cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int32_t* info,
@@ -155,12 +170,12 @@ bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_
     if (mis || (reinterpret_cast<uintptr_t>(info) & 3u) || (reinterpret_cast<uintptr_t>(counters) & 7u))
         return BED_ERR_INVALID_ARG;
     if (A == V) return BED_ERR_INVALID_ARG;
-    Plan P;
-    if (!build_plan(n, prm.leaf_size, &P)) return BED_ERR_INVALID_ARG;
+    const Plan* P = cached_plan(n, prm.leaf_size);
+    if (!P) return BED_ERR_INVALID_ARG;
     // TMA bulk staging needs a 16-byte aligned source and a size that is a multiple of 16 bytes for
     // every matrix: A 16-byte aligned and n even.
     const bool bulk = ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && (n % 2 == 0);
-    const cudaError_t e = launch_eigh(nmax, g, A, W, V, info, batch, P, kp, counters, bulk, stream);
+    const cudaError_t e = launch_eigh(nmax, g, A, W, V, info, batch, *P, kp, counters, bulk, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     return BED_OK;
 }

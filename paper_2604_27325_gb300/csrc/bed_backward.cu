@@ -7,6 +7,7 @@
 // dv_i = sum_{j != i} v_j v_j^T dA v_i / (W_i - W_j)); gA is the gradient over symmetric
 // perturbations of A. One thread block per matrix, the three products in shared memory with FP32
 // FMA: thread (column j, row group g) owns rows g, g + G, ... of column j of each product.
+#include <atomic>
 #include <cfloat>
 
 #include <cuda_runtime.h>
@@ -135,8 +136,15 @@ static cudaError_t launch_bwd(const float* W, const float* V, const float* gW, c
     constexpr int G = 4;
     const size_t smem = sizeof(BwdSmem<NMAX>);
     auto kern = eigh_backward_kernel<NMAX, G>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    static std::atomic<unsigned long long> configured{0};  // per device, set on its first launch
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (!(configured.load(std::memory_order_acquire) & (1ull << (dev & 63)))) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        configured.fetch_or(1ull << (dev & 63), std::memory_order_release);
+    }
     const unsigned grid = static_cast<unsigned>(batch < 2147483647LL ? batch : 2147483647LL);
     kern<<<grid, NMAX * G, smem, stream>>>(W, V, gW, gV, gA, batch, n, gap_eps);
     return cudaGetLastError();

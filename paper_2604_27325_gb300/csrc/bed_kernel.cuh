@@ -21,6 +21,7 @@
 // group; a1 and a7 use their own register tilings, described where they run.
 #pragma once
 
+#include <atomic>
 #include <cfloat>
 #include <cstdint>
 
@@ -1465,12 +1466,21 @@ cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int
 {
     const size_t smem = sizeof(Smem<NMAX, G>);
     auto kern = eigh_kernel<NMAX, G>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
+    // the function attributes are per device: set them on the first launch there (setting them again
+    // from a racing thread is harmless), keeping later launches to the launch itself
+    static std::atomic<unsigned long long> configured{0};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
-    if (err != cudaSuccess) return err;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured.load(std::memory_order_acquire) & bit)) {
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (err != cudaSuccess) return err;
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   cudaSharedmemCarveoutMaxShared);
+        if (err != cudaSuccess) return err;
+        configured.fetch_or(bit, std::memory_order_release);
+    }
     const int64_t max_grid = 2147483647LL;
     const unsigned grid = static_cast<unsigned>(batch < max_grid ? batch : max_grid);
     kern<<<grid, NMAX * G, smem, stream>>>(A, W, V, info, batch, P, kp, counters, bulk ? 1 : 0);
