@@ -485,6 +485,7 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
             if (f > 0.f) U = h;
             else if (f < 0.f) L = h;
             else { done = true; r.conv = true; }
+            float hev = h;  // the point just evaluated, relative to the current origin
             if (state == 0) {
                 if (!done && !top && f < 0.f) {
                     // root in the upper half of (d_q, d_{q+1}): measure it from d_{q+1}
@@ -492,6 +493,7 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
                     o = q + 1;
                     L -= sh;
                     U = 0.f;
+                    hev = h - sh;
                 }
                 state = 1;
             } else {
@@ -499,8 +501,19 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
             }
             if (!done) {
                 if ((U - L) < kp.sec_eps * width0 || nsec >= kp.max_sec) {
+                    // Halley starts from the root of the one-pole model of f at the last point (the
+                    // same model as its fallback below) when that lies in the bracket, else the midpoint
                     state = 2;
-                    h = 0.5f * (L + U);
+                    float hn = 0.5f * (L + U);
+                    if (hev != 0.f) {
+                        const float rz = rho * dz[o].y;
+                        const float g = f + rz / hev;
+                        if (g != 0.f) {
+                            const float he = rz / g;
+                            if ((he > L) && (top ? he <= U : he < U)) hn = he;
+                        }
+                    }
+                    h = hn;
                 } else {
                     h = fmaf(U - L, kinv, L);  // Eq. (16)
                 }
