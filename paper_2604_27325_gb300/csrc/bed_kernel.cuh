@@ -39,7 +39,7 @@ template <int NMAX, int G>
 struct Smem {
     static constexpr int LD = NMAX + 1;  // odd stride: column walks hit distinct banks
     static constexpr int NB = NMAX / 2;  // merges per level, at most
-    alignas(16) float A[NMAX * LD];  // matrix; after a1 the reflectors, transposed (yt_index)
+    alignas(16) float A[NMAX * LD];  // the reflectors of a1, transposed (yt_index)
     float Q[NMAX * LD + 3 * LD];      // eigenvectors of the current blocks (block diagonal); P8 tiles read
                                       // up to 3 rows past the last one
     alignas(16) float M[NMAX * LD + 8];  // staging of A[b]; merge workspace (rows = sorted poles); a8
@@ -665,13 +665,6 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         S.out_v = Vb;
         S.out_info = info_b;
     }
-    for (int i = warp; i < n; i += NW)
-        for (int j = lane; j <= i; j += 32) {
-            const float x = S.M[i * n + j] * scale;
-            S.A[i * LD + j] = x;
-            S.A[j * LD + i] = x;
-        }
-    team_sync<NT>(bar_id);
 
     // ---------------- a1: Householder tridiagonalization ------------------------------------
     // Column-owned register tiles, one barrier per reflector. Warp w keeps columns
@@ -698,12 +691,13 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         const int tr = lane / NTC, tc = lane % NTC;
         const int i0 = tr * TR, j0 = warp * WC + tc * TC;
         float a[TR][TC];
+        // the tile comes straight from the staged input (row-major n x n, lower triangle read), scaled
 #pragma unroll
         for (int ii = 0; ii < TR; ++ii)
 #pragma unroll
             for (int jj = 0; jj < TC; ++jj) {
                 const int i = i0 + ii, j = j0 + jj;
-                a[ii][jj] = (i < n && j < n) ? S.A[i * LD + j] : 0.f;
+                a[ii][jj] = (i < n && j < n) ? S.M[(j <= i) ? (i * n + j) : (j * n + i)] * scale : 0.f;
             }
         // step 0 reads buffer 1: p = v = 0 and column 0 of A
         for (int i = tid; i < NMAX; i += NT) {
@@ -712,9 +706,9 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             S.hy[0][i] = 0.f;
             S.hp[1][i] = 0.f;
             S.hu[1][i] = 0.f;
-            S.hy[1][i] = (i < n) ? S.A[i * LD] : 0.f;
+            S.hy[1][i] = (i < n) ? S.M[i * n] * scale : 0.f;
         }
-        team_sync<NT>(bar_id);  // every tile is loaded before row k of S.A takes reflector k
+        team_sync<NT>(bar_id);  // every tile is loaded before the merge phases reuse the staging area
         const int wlast = (n - 1) / WC;  // owns column n - 1: active in every step; stores reflectors
         float tau_prev = 0.f;
         for (int k = 0; k + 2 < n; ++k) {
