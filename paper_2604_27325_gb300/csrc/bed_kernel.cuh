@@ -61,7 +61,7 @@ struct Smem {
         };
     };
     float sgn[NMAX];
-    float brho[NB], bnz[NB], btol[NB], bsc[NB];  // per merge of a level: |beta|, |z|, tolerance, scale
+    float brho[NB], btol[NB], bsc[NB];  // per merge of a level: |beta|, tolerance, scale
     int rank[NMAX];   // column c of the children -> its sorted position
     int inv[NMAX];    // compacted index -> sorted position
     int org[NMAX];    // root -> compacted index of the pole it is measured from
@@ -915,7 +915,8 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             mid = plan.m_mid[bi];
             hi = plan.m_hi[bi];
         }
-        // P1: z (Eq. (5)), pole order, block scalars
+        // P1: z (Eq. (5)), pole order, block scalars, negligible couplings. Every group of the merge
+        // forms the block scalars from the same sums in the same order, so all agree exactly
         {
             const int c = pos;
             float zc = 0.f, kc = 0.f;
@@ -940,17 +941,20 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             nz2 = gsum<G>(nz2);
             dmax = gmax<G>(dmax);
             if (act && sub == 0) {
+                const float rho = fabsf(S.e[mid - 1]);
+                const float bscale = fmaxf(dmax, rho * nz2);
+                const float nz = sqrt_approx(nz2);
+                const float tol = kp.defl_c * kU * bscale;
                 S.rank[c] = lo + p;
                 S.ds[lo + p] = S.lam[c];
                 S.zs[lo + p] = zc;
+                S.defl[lo + p] = (rho * fabsf(zc) * nz <= tol);  // deflation of a negligible coupling
+                S.rotj[lo + p] = -1;
                 if (c == lo) {
-                    const float rho = fabsf(S.e[mid - 1]);
-                    const float bscale = fmaxf(dmax, rho * nz2);
                     int bex = 0;
                     if (bscale > 0.f) frexpf(bscale, &bex);
                     S.brho[lb] = rho;
-                    S.bnz[lb] = sqrt_approx(nz2);
-                    S.btol[lb] = kp.defl_c * kU * bscale;
+                    S.btol[lb] = tol;
                     S.bsc[lb] = ldexpf(1.f, -bex);
                     S.brot[lb] = 0;
                 }
@@ -958,70 +962,17 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         }
         if (tid == 0) S.flag_rot = 0;
         team_sync<NT>(bar_id);
-        // P2: deflation of negligible couplings; detect close-pole pairs
-        if (act && sub == 0) {
-            const int t = pos;
-            const float rho = S.brho[lb], nz = S.bnz[lb], tol = S.btol[lb];
-            const float zp = S.zs[t];
-            const int dfl = (rho * fabsf(zp) * nz <= tol);
-            S.defl[t] = dfl;
-            S.rotj[t] = -1;
-            if (!dfl) {
-                int j = t + 1;
-                while (j < hi && rho * fabsf(S.zs[j]) * nz <= tol) ++j;
-                if (j < hi) {
-                    // c s = zp zj / (zp^2 + zj^2); the test is loosened by 2 so that no pair the exact
-                    // test of P3 (with hypot) would rotate is missed
-                    const float zj = S.zs[j];
-                    const float cs = zp * zj * rcp_approx(fmaf(zp, zp, zj * zj));
-                    if (fabsf((S.ds[j] - S.ds[t]) * cs) <= 2.f * tol) {
-                        S.brot[lb] = 1;
-                        S.flag_rot = 1;
-                    }
-                }
-            }
-        }
-        team_sync<NT>(bar_id);
-        // P3: close-pole Givens deflation, one pass in pole order (rare)
-        if (S.flag_rot) {
-            if (act && sub == 0 && pos == lo && S.brot[lb]) {
-                const float tol = S.btol[lb];
-                int pj = -1;
-                for (int p = lo; p < hi; ++p) {
-                    if (S.defl[p]) continue;
-                    if (pj < 0) {
-                        pj = p;
-                        continue;
-                    }
-                    const float r = hypotf(S.zs[pj], S.zs[p]);
-                    const float cc = S.zs[p] / r, ss = S.zs[pj] / r;
-                    if (fabsf((S.ds[p] - S.ds[pj]) * cc * ss) <= tol) {
-                        const float a = S.ds[pj], bb = S.ds[p];
-                        S.ds[pj] = fmaf(cc * cc, a, ss * ss * bb);
-                        S.ds[p] = fmaf(ss * ss, a, cc * cc * bb);
-                        S.zs[p] = r;
-                        S.zs[pj] = 0.f;
-                        S.defl[pj] = 1;
-                        S.rotj[pj] = p;
-                        S.rc[pj] = cc;
-                        S.rs[pj] = ss;
-                    }
-                    pj = p;
-                }
-            }
-            team_sync<NT>(bar_id);
-        }
         // P4: compaction, non-deflated poles first (ascending). The secular problem of the block is
         // scaled exactly by a power of two to unit size: the derivatives of f grow like
         // 1/(d - lambda)^3 and would overflow FP32 for blocks whose spectrum is far below 1
-        {
+        auto compact = [&]() {
             const int t = pos;
             int nb = 0, K = 0;
             if (act)
-                for (int p = lo + sub; p < hi; p += G) {
-                    const int nd = !S.defl[p];
+                for (int p2 = lo + sub; p2 < hi; p2 += G) {
+                    const int nd = !S.defl[p2];
                     K += nd;
-                    nb += (p < t) & nd;
+                    nb += (p2 < t) & nd;
                 }
             nb = gsumi<G>(nb);
             K = gsumi<G>(K);
@@ -1030,13 +981,61 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 S.inv[lo + q] = t;
                 S.cdz[lo + q] = make_float2(S.ds[t] * S.bsc[lb], S.zs[t] * S.zs[t]);
                 S.cz[lo + q] = S.zs[t];
-                if (t == lo) {
-                    S.bK[lb] = K;
-                    atomicAdd(&S.deflated, static_cast<unsigned>(hi - lo - K));
+                if (t == lo) S.bK[lb] = K;
+            }
+        };
+        // P2 (detect close-pole pairs) with the compaction in the same phase; in the rare case that a
+        // pair is found, P3 rotates and the compaction is redone
+        if (act && sub == 0 && !S.defl[pos]) {
+            const int t = pos;
+            const float tol = S.btol[lb];
+            const float zp = S.zs[t];
+            int j = t + 1;
+            while (j < hi && S.defl[j]) ++j;
+            if (j < hi) {
+                // c s = zp zj / (zp^2 + zj^2); the test is loosened by 2 so that no pair the exact
+                // test of P3 (with hypot) would rotate is missed
+                const float zj = S.zs[j];
+                const float cs = zp * zj * rcp_approx(fmaf(zp, zp, zj * zj));
+                if (fabsf((S.ds[j] - S.ds[t]) * cs) <= 2.f * tol) {
+                    S.brot[lb] = 1;
+                    S.flag_rot = 1;
                 }
             }
         }
+        compact();
         team_sync<NT>(bar_id);
+        // P3: close-pole Givens deflation, one pass in pole order (rare)
+        if (S.flag_rot) {
+            if (act && sub == 0 && pos == lo && S.brot[lb]) {
+                const float tol = S.btol[lb];
+                int pj = -1;
+                for (int p2 = lo; p2 < hi; ++p2) {
+                    if (S.defl[p2]) continue;
+                    if (pj < 0) {
+                        pj = p2;
+                        continue;
+                    }
+                    const float r = hypotf(S.zs[pj], S.zs[p2]);
+                    const float cc = S.zs[p2] / r, ss = S.zs[pj] / r;
+                    if (fabsf((S.ds[p2] - S.ds[pj]) * cc * ss) <= tol) {
+                        const float a2 = S.ds[pj], bb = S.ds[p2];
+                        S.ds[pj] = fmaf(cc * cc, a2, ss * ss * bb);
+                        S.ds[p2] = fmaf(ss * ss, a2, cc * cc * bb);
+                        S.zs[p2] = r;
+                        S.zs[pj] = 0.f;
+                        S.defl[pj] = 1;
+                        S.rotj[pj] = p2;
+                        S.rc[pj] = cc;
+                        S.rs[pj] = ss;
+                    }
+                    pj = p2;
+                }
+            }
+            team_sync<NT>(bar_id);
+            compact();
+            team_sync<NT>(bar_id);
+        }
         // P5: secular roots, G lanes per root
         {
             int K = 0, q = 0;
@@ -1048,6 +1047,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 rho = S.brho[lb] * sc;
             }
             const bool part = act && (q < K);
+            if (act && q == 0 && sub == 0) atomicAdd(&S.deflated, static_cast<unsigned>(hi - lo - K));
             const RootOut r = secular_root<G>(S.cdz + lo, K, q, rho, kp, part, sub);
             if (sub == 0) {
                 if (part) {

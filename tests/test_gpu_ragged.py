@@ -108,3 +108,16 @@ def test_ragged_counters_and_empty():
     rb0 = B.RaggedBatch([])
     rb0.solve()
     torch.cuda.synchronize()
+
+
+def test_ragged_workload_full_size_graph_replay_against_oracle():
+    """The ragged workload at its full size (8192 matrices, n ~ U{4..64}) in the configuration the
+    benchmark times (tuned table, CUDA-graph replay), every matrix against the oracle."""
+    from paper_2604_27325_gb300 import autotune
+
+    mats, ns = wl.ragged(8192)
+    rb = B.RaggedBatch(ns, tuning=autotune.load()).load(mats)
+    rb.capture()
+    rb.replay()
+    torch.cuda.synchronize()
+    check_against_oracle(mats, rb.results(), rb.info.cpu().numpy()[: rb.count], "ragged 8192")
