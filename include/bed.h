@@ -112,6 +112,26 @@ bed_status bed_eigh_f32_counted(const float* A, float* W, float* V, int32_t* inf
                                 cudaStream_t stream);
 
 /*
+ * End-to-end solve of a uniform batch held in HOST memory (no counterpart in the paper: the
+ * copy-in / solve / copy-out pipeline of a caller whose matrices live on the host).
+ *   A_host, W_host, V_host, info_host  host buffers in the layouts of bed_eigh_f32 (info_host may be
+ *            NULL); they must be page-locked (cudaHostAlloc / cudaHostRegister) for the copies to run
+ *            asynchronously and overlap
+ *   A_dev [batch*n*n], W_dev [batch*n], V_dev [batch*n*n], info_dev [batch] (may be NULL)
+ *            caller-owned device scratch; the library allocates nothing
+ *   chunks   the batch is cut into this many pieces (0: automatic, two from 256 matrices on, else one);
+ *            piece c is copied in, solved and copied out on stream s[c % 2], so that the copies of one
+ *            piece overlap the solve of another. s0 and s1 may be the same stream (no overlap).
+ * Returns after enqueuing everything (argument errors before anything is enqueued, as bed_eigh_f32);
+ * the results are in host memory once both streams have reached this call's work. The host buffers
+ * must stay valid until then.
+ */
+bed_status bed_eigh_f32_host(const float* A_host, float* W_host, float* V_host, int32_t* info_host,
+                             int64_t batch, int n, const bed_params* p, float* A_dev, float* W_dev,
+                             float* V_dev, int32_t* info_dev, int chunks, cudaStream_t s0,
+                             cudaStream_t s1);
+
+/*
  * Ragged batches: matrices of mixed size in one persistent launch (Sec. 2.1 notes that dividing turns a
  * batch of B matrices into B*R blocks; here blocks of all sizes share the GPU in one launch).
  *

@@ -71,6 +71,7 @@ EXPORTED = [
     "bed_default_params",
     "bed_eigh_f32",
     "bed_eigh_f32_counted",
+    "bed_eigh_f32_host",
     "bed_eigh_backward_f32",
     "bed_eigh_ragged_f32",
     "bed_eigh_ragged_f32_noalloc",
@@ -107,6 +108,9 @@ def lib() -> C.CDLL:
             L.bed_eigh_f32.restype = C.c_int
             L.bed_eigh_f32_counted.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.POINTER(bed_params), vp, vp]
             L.bed_eigh_f32_counted.restype = C.c_int
+            L.bed_eigh_f32_host.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.POINTER(bed_params), vp, vp, vp,
+                                            vp, C.c_int, vp, vp]
+            L.bed_eigh_f32_host.restype = C.c_int
             L.bed_max_n.argtypes = []
             L.bed_max_n.restype = C.c_int
             L.bed_status_string.argtypes = [C.c_int]
@@ -162,6 +166,14 @@ def bed_eigh_f32(A_ptr: int, W_ptr: int, V_ptr: int, info_ptr: int | None, batch
     """Raw call: device pointers as integers; returns the bed_status code."""
     return lib().bed_eigh_f32(A_ptr, W_ptr, V_ptr, info_ptr, batch, n,
                               C.byref(params) if params is not None else None, stream)
+
+
+def bed_eigh_f32_host(A_host: int, W_host: int, V_host: int, info_host: int | None, batch: int, n: int,
+                      params: bed_params | None, A_dev: int, W_dev: int, V_dev: int, info_dev: int | None,
+                      chunks: int = 0, s0: int = 0, s1: int = 0) -> int:
+    return lib().bed_eigh_f32_host(A_host, W_host, V_host, info_host, batch, n,
+                                   C.byref(params) if params is not None else None, A_dev, W_dev, V_dev, info_dev,
+                                   chunks, s0, s1)
 
 
 def bed_eigh_f32_counted(A_ptr: int, W_ptr: int, V_ptr: int, info_ptr: int | None, batch: int, n: int,
@@ -455,14 +467,15 @@ def _streams(dev: torch.device, k: int):
 
 
 def batched_eigh_many(mats, params: bed_params | None = None, check: bool = False,
-                      return_info: bool = False):
+                      return_info: bool = False, host_chunks: int = 0):
     """Eigendecompositions of several uniform batches: a list of FP32 tensors ``[..., n_i, n_i]``, all on
     the CPU or all on one CUDA device.
 
     Each batch gets one launch on its own stream, forked from the current stream and joined back to it,
-    so that batches of different n run side by side on the GPU instead of one after another. For CPU
-    tensors each stream also carries its batch's copy to the device and the copies of its results back,
-    overlapping the other batches' kernels; the call returns once all results are in host memory.
+    so that batches of different n run side by side on the GPU instead of one after another. CPU tensors
+    go through ``bed_eigh_f32_host``: each batch is copied in, solved and copied out in pieces pipelined
+    over two streams of its own, so that copies overlap solves; the call returns once all results are in
+    (page-locked) host memory.
     Returns a list of ``(W, V)`` (``(W, V, info)`` with ``return_info``), in the order of ``mats``."""
     mats = list(mats)
     if not mats:
@@ -481,18 +494,52 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
     # largest n first: its launch is the longest and should start first
     order = sorted(range(len(mats)), key=lambda i: -mats[i].shape[-1])
     outs = [None] * len(mats)
-    for i, s in zip(order, _streams(dev, len(mats))):
-        s.wait_event(fork)
-        with torch.cuda.stream(s):
-            outs[i] = _eigh_enqueue(mats[i], params, None)
-        join = torch.cuda.Event()
-        join.record(s)
-        cur.wait_event(join)
-        if not host:
+    side = _streams(dev, 2 * len(mats) if host else len(mats))
+    for k, i in enumerate(order):
+        if host:
+            # copy-in / solve / copy-out pipelined in pieces over two streams (bed_eigh_f32_host)
+            s0, s1 = side[2 * k], side[2 * k + 1]
+            s0.wait_event(fork)
+            s1.wait_event(fork)
+            A = mats[i]
+            if A.dtype != torch.float32 or A.dim() < 2 or A.shape[-1] != A.shape[-2]:
+                raise ValueError("batched_eigh_many expects float32 [..., n, n] batches")
+            lead, n = A.shape[:-2], A.shape[-1]
+            Ah = A.reshape(-1, n, n).contiguous()
+            if not Ah.is_pinned():
+                Ah = Ah.pin_memory()
+            b = Ah.shape[0]
+            Wh = torch.empty((b, n), dtype=torch.float32, pin_memory=True)
+            Vh = torch.empty((b, n, n), dtype=torch.float32, pin_memory=True)
+            Ih = torch.empty((b,), dtype=torch.int32, pin_memory=True)
+            with torch.cuda.stream(s0):
+                Ad = torch.empty((b, n, n), dtype=torch.float32, device=dev)
+                Wd = torch.empty((b, n), dtype=torch.float32, device=dev)
+                Vd = torch.empty((b, n, n), dtype=torch.float32, device=dev)
+                Id = torch.empty((b,), dtype=torch.int32, device=dev)
+            for t in (Ad, Wd, Vd, Id):
+                t.record_stream(s1)
+            _check(bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, params,
+                                     Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), Id.data_ptr(), host_chunks,
+                                     s0.cuda_stream, s1.cuda_stream))
+            outs[i] = (Wh, Vh, Ih, True, lead, n, (Ah, Ad, Wd, Vd, Id))
+            for s in (s0, s1):
+                join = torch.cuda.Event()
+                join.record(s)
+                cur.wait_event(join)
+        else:
+            s = side[k]
+            s.wait_event(fork)
+            with torch.cuda.stream(s):
+                outs[i] = _eigh_enqueue(mats[i], params, None)
+            join = torch.cuda.Event()
+            join.record(s)
+            cur.wait_event(join)
             for t in outs[i][:3]:
                 t.record_stream(cur)
     if host:
         cur.synchronize()
+        outs = [o[:6] for o in outs]
     return [_eigh_finish(o, check, return_info) for o in outs]
 
 

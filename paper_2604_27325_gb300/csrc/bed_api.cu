@@ -268,6 +268,51 @@ bed_status bed_eigh_f32_counted(const float* A, float* W, float* V, int32_t* inf
     return bed::eigh_common(A, W, V, info, batch, n, p, counters, stream);
 }
 
+bed_status bed_eigh_f32_host(const float* A_host, float* W_host, float* V_host, int32_t* info_host,
+                             int64_t batch, int n, const bed_params* p, float* A_dev, float* W_dev,
+                             float* V_dev, int32_t* info_dev, int chunks, cudaStream_t s0,
+                             cudaStream_t s1)
+{
+    if (n < 1 || n > bed::kMaxN) return BED_ERR_UNSUPPORTED_N;
+    if (batch < 0 || chunks < 0) return BED_ERR_INVALID_ARG;
+    if (batch == 0) return BED_OK;
+    if (!A_host || !W_host || !V_host || !A_dev || !W_dev || !V_dev) return BED_ERR_INVALID_ARG;
+    if ((info_host == nullptr) != (info_dev == nullptr)) return BED_ERR_INVALID_ARG;
+    {
+        // validate the parameters and the device buffers once, before anything is enqueued
+        bed_params prm;
+        bed::KParams kp;
+        if (!bed::make_kparams(p, &prm, &kp)) return BED_ERR_INVALID_ARG;
+        const uintptr_t mis = (reinterpret_cast<uintptr_t>(A_dev) | reinterpret_cast<uintptr_t>(W_dev) |
+                               reinterpret_cast<uintptr_t>(V_dev) | reinterpret_cast<uintptr_t>(info_dev)) & 3u;
+        if (mis || A_dev == V_dev) return BED_ERR_INVALID_ARG;
+    }
+    // automatic: two pieces (one per stream) from 256 matrices on; more pieces measured slower (each
+    // piece is a smaller launch and four more copies)
+    int64_t nc = chunks ? chunks : (batch >= 256 ? 2 : 1);
+    if (nc > batch) nc = batch;
+    const size_t nn = static_cast<size_t>(n) * n;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t b0 = batch * c / nc, b1 = batch * (c + 1) / nc, nb = b1 - b0;
+        if (nb == 0) continue;
+        cudaStream_t s = (c & 1) ? s1 : s0;
+        cudaError_t e = cudaMemcpyAsync(A_dev + b0 * nn, A_host + b0 * nn, nb * nn * sizeof(float),
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bed::cuda_fail(e);
+        const bed_status st = bed::eigh_common(A_dev + b0 * nn, W_dev + b0 * n, V_dev + b0 * nn,
+                                               info_dev ? info_dev + b0 : nullptr, nb, n, p, nullptr, s);
+        if (st != BED_OK) return st;
+        e = cudaMemcpyAsync(W_host + b0 * n, W_dev + b0 * n, nb * n * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(V_host + b0 * nn, V_dev + b0 * nn, nb * nn * sizeof(float),
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && info_host)
+            e = cudaMemcpyAsync(info_host + b0, info_dev + b0, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return bed::cuda_fail(e);
+    }
+    return BED_OK;
+}
+
 bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count,
                                        float* W, const int64_t* w_offsets, float* V, int32_t* info,
                                        const bed_params* p, const bed_ragged_tuning* tuning,

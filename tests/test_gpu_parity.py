@@ -251,3 +251,31 @@ def test_uniform_covariance_with_ql_leaves(n):
     W, V, info = run_gpu(A, B.make_params(leaf_size=8))
     Wo, Vo = run_oracle(A)
     assert_parity(A, W, V, info, Wo, Vo, f"covariance 512 x {n}, leaf 8")
+
+
+@pytest.mark.parametrize("chunks", [0, 1, 3, 7])
+def test_host_entry_point_pipelined(chunks):
+    """bed_eigh_f32_host (copy-in, solve, copy-out in pieces over two streams) gives the results of
+    bed_eigh_f32 on the same matrices, bitwise, for any cut of the batch."""
+    A = wl.covariance(300, 37, seed=77)
+    b, n = A.shape[0], A.shape[-1]
+    Ah = torch.from_numpy(A).pin_memory()
+    Wh = torch.full((b, n), -7.0).pin_memory()
+    Vh = torch.full((b, n, n), -7.0).pin_memory()
+    Ih = torch.full((b,), -1, dtype=torch.int32).pin_memory()
+    Ad = torch.empty(b, n, n, device="cuda")
+    Wd = torch.empty(b, n, device="cuda")
+    Vd = torch.empty(b, n, n, device="cuda")
+    Id = torch.empty(b, dtype=torch.int32, device="cuda")
+    s0, s1 = torch.cuda.Stream(), torch.cuda.Stream()
+    st = B.bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, None, Ad.data_ptr(),
+                             Wd.data_ptr(), Vd.data_ptr(), Id.data_ptr(), chunks, s0.cuda_stream, s1.cuda_stream)
+    assert st == B.BED_OK
+    torch.cuda.synchronize()
+    W, V, info = run_gpu(A)
+    assert np.array_equal(Wh.numpy(), W) and np.array_equal(Vh.numpy(), V) and np.array_equal(Ih.numpy(), info)
+    # argument errors come back before anything is enqueued
+    assert B.bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, None,
+                               Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), None, 0, 0, 0) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), None, b, 65, None,
+                               Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), None, 0, 0, 0) == B.BED_ERR_UNSUPPORTED_N
