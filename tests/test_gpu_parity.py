@@ -279,3 +279,24 @@ def test_host_entry_point_pipelined(chunks):
                                Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), None, 0, 0, 0) == B.BED_ERR_INVALID_ARG
     assert B.bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), None, b, 65, None,
                                Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), None, 0, 0, 0) == B.BED_ERR_UNSUPPORTED_N
+
+
+@pytest.mark.parametrize("n", [5, 16, 40, 64])
+def test_power_of_two_scaling_is_exact(n):
+    """The kernel scales every matrix by a power of two before solving and back after: A 2^e gives
+    exactly W 2^e and the same V, over the whole exponent range."""
+    A = wl.covariance(8, n, seed=55)
+    W0, V0, i0 = run_gpu(A)
+    for e in (-100, -60, 60, 120):  # inputs and results stay in the normal range
+        W, V, info = run_gpu((A * np.float32(2.0 ** e)).astype(np.float32))
+        assert np.all(info == 0)
+        assert np.array_equal(W, W0 * np.float32(2.0 ** e)) and np.array_equal(V, V0)
+
+
+def test_large_and_small_magnitudes_hold_tolerance():
+    for s in (1e-30, 1e30):
+        A = (wl.covariance(8, 48, seed=56).astype(np.float64) * s).astype(np.float32)
+        W, V, info = run_gpu(A)
+        Wo, Vo = run_oracle(A)
+        assert_parity(A, W, V, info, Wo, Vo, f"scale {s}")
+
