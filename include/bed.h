@@ -132,6 +132,22 @@ bed_status bed_eigh_f32_host(const float* A_host, float* W_host, float* V_host, 
                              cudaStream_t s1);
 
 /*
+ * Zero-copy solve of a uniform batch held in PAGE-LOCKED HOST memory (no counterpart in the paper:
+ * the input/output path of a caller whose matrices live on the host). The kernel reads every matrix
+ * straight from A_host and writes W_host, V_host, info_host over the host-device link through the
+ * unified address space, so that each matrix's transfers overlap the solve of the others and no
+ * device buffer or copy is involved.
+ *   A_host, W_host, V_host, info_host  host buffers in the layouts of bed_eigh_f32 (info_host may be
+ *            NULL); each must lie inside one page-locked allocation of the current CUDA context
+ *            (cudaHostAlloc, cudaMallocHost or cudaHostRegister), checked with cudaPointerGetAttributes
+ *            on its first and last byte: BED_ERR_INVALID_ARG otherwise, before anything is enqueued.
+ * Returns after enqueuing the launch on `stream`; the results are in host memory once the stream has
+ * reached it. The buffers must stay valid and untouched by the host until then.
+ */
+bed_status bed_eigh_f32_pinned(const float* A_host, float* W_host, float* V_host, int32_t* info_host,
+                               int64_t batch, int n, const bed_params* p, cudaStream_t stream);
+
+/*
  * Ragged batches: matrices of mixed size in one persistent launch (Sec. 2.1 notes that dividing turns a
  * batch of B matrices into B*R blocks; here blocks of all sizes share the GPU in one launch).
  *

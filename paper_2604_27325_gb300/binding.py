@@ -72,6 +72,7 @@ EXPORTED = [
     "bed_eigh_f32",
     "bed_eigh_f32_counted",
     "bed_eigh_f32_host",
+    "bed_eigh_f32_pinned",
     "bed_eigh_backward_f32",
     "bed_eigh_ragged_f32",
     "bed_eigh_ragged_f32_noalloc",
@@ -111,6 +112,8 @@ def lib() -> C.CDLL:
             L.bed_eigh_f32_host.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.POINTER(bed_params), vp, vp, vp,
                                             vp, C.c_int, vp, vp]
             L.bed_eigh_f32_host.restype = C.c_int
+            L.bed_eigh_f32_pinned.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.POINTER(bed_params), vp]
+            L.bed_eigh_f32_pinned.restype = C.c_int
             L.bed_max_n.argtypes = []
             L.bed_max_n.restype = C.c_int
             L.bed_status_string.argtypes = [C.c_int]
@@ -166,6 +169,12 @@ def bed_eigh_f32(A_ptr: int, W_ptr: int, V_ptr: int, info_ptr: int | None, batch
     """Raw call: device pointers as integers; returns the bed_status code."""
     return lib().bed_eigh_f32(A_ptr, W_ptr, V_ptr, info_ptr, batch, n,
                               C.byref(params) if params is not None else None, stream)
+
+
+def bed_eigh_f32_pinned(A_host: int, W_host: int, V_host: int, info_host: int | None, batch: int, n: int,
+                        params: bed_params | None = None, stream: int = 0) -> int:
+    return lib().bed_eigh_f32_pinned(A_host, W_host, V_host, info_host, batch, n,
+                                     C.byref(params) if params is not None else None, stream)
 
 
 def bed_eigh_f32_host(A_host: int, W_host: int, V_host: int, info_host: int | None, batch: int, n: int,
@@ -473,9 +482,10 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
 
     Each batch gets one launch on its own stream, forked from the current stream and joined back to it,
     so that batches of different n run side by side on the GPU instead of one after another. CPU tensors
-    go through ``bed_eigh_f32_host``: each batch is copied in, solved and copied out in pieces pipelined
-    over two streams of its own, so that copies overlap solves; the call returns once all results are in
-    (page-locked) host memory.
+    are solved in place in page-locked host memory (``bed_eigh_f32_pinned``: the kernel reads the
+    matrices and writes the results across the host-device link, no device buffers); with
+    ``host_chunks > 0`` they go through ``bed_eigh_f32_host`` instead (copy in, solve and copy out in that
+    many pieces over two streams). Host results are returned once they are in (page-locked) host memory.
     Returns a list of ``(W, V)`` (``(W, V, info)`` with ``return_info``), in the order of ``mats``."""
     mats = list(mats)
     if not mats:
@@ -494,13 +504,11 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
     # largest n first: its launch is the longest and should start first
     order = sorted(range(len(mats)), key=lambda i: -mats[i].shape[-1])
     outs = [None] * len(mats)
-    side = _streams(dev, 2 * len(mats) if host else len(mats))
+    copies = host and host_chunks > 0
+    side = _streams(dev, 2 * len(mats) if copies else len(mats))
+    keep = []  # device scratch of the copy path, alive until the final synchronize
     for k, i in enumerate(order):
         if host:
-            # copy-in / solve / copy-out pipelined in pieces over two streams (bed_eigh_f32_host)
-            s0, s1 = side[2 * k], side[2 * k + 1]
-            s0.wait_event(fork)
-            s1.wait_event(fork)
             A = mats[i]
             if A.dtype != torch.float32 or A.dim() < 2 or A.shape[-1] != A.shape[-2]:
                 raise ValueError("batched_eigh_many expects float32 [..., n, n] batches")
@@ -512,18 +520,32 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
             Wh = torch.empty((b, n), dtype=torch.float32, pin_memory=True)
             Vh = torch.empty((b, n, n), dtype=torch.float32, pin_memory=True)
             Ih = torch.empty((b,), dtype=torch.int32, pin_memory=True)
-            with torch.cuda.stream(s0):
-                Ad = torch.empty((b, n, n), dtype=torch.float32, device=dev)
-                Wd = torch.empty((b, n), dtype=torch.float32, device=dev)
-                Vd = torch.empty((b, n, n), dtype=torch.float32, device=dev)
-                Id = torch.empty((b,), dtype=torch.int32, device=dev)
-            for t in (Ad, Wd, Vd, Id):
-                t.record_stream(s1)
-            _check(bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, params,
-                                     Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), Id.data_ptr(), host_chunks,
-                                     s0.cuda_stream, s1.cuda_stream))
-            outs[i] = (Wh, Vh, Ih, True, lead, n, (Ah, Ad, Wd, Vd, Id))
-            for s in (s0, s1):
+            outs[i] = (Wh, Vh, Ih, True, lead, n)
+            keep.append(Ah)
+            if copies:
+                # copy-in / solve / copy-out pipelined in pieces over two streams (bed_eigh_f32_host)
+                s0, s1 = side[2 * k], side[2 * k + 1]
+                s0.wait_event(fork)
+                s1.wait_event(fork)
+                with torch.cuda.stream(s0):
+                    Ad = torch.empty((b, n, n), dtype=torch.float32, device=dev)
+                    Wd = torch.empty((b, n), dtype=torch.float32, device=dev)
+                    Vd = torch.empty((b, n, n), dtype=torch.float32, device=dev)
+                    Id = torch.empty((b,), dtype=torch.int32, device=dev)
+                for t in (Ad, Wd, Vd, Id):
+                    t.record_stream(s1)
+                keep.append((Ad, Wd, Vd, Id))
+                _check(bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, params,
+                                         Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), Id.data_ptr(), host_chunks,
+                                         s0.cuda_stream, s1.cuda_stream))
+                used = (s0, s1)
+            else:
+                s = side[k]
+                s.wait_event(fork)
+                _check(bed_eigh_f32_pinned(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, params,
+                                           s.cuda_stream))
+                used = (s,)
+            for s in used:
                 join = torch.cuda.Event()
                 join.record(s)
                 cur.wait_event(join)
@@ -539,7 +561,7 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
                 t.record_stream(cur)
     if host:
         cur.synchronize()
-        outs = [o[:6] for o in outs]
+        del keep
     return [_eigh_finish(o, check, return_info) for o in outs]
 
 

@@ -1,5 +1,6 @@
 // C ABI of the batched eigensolver: argument validation, the divide-tree plan, launch selection.
 #include <cfloat>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -139,7 +140,7 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
 }
 
 bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
-                       const bed_params* p, bed_counters* counters, cudaStream_t stream)
+                       const bed_params* p, bed_counters* counters, cudaStream_t stream, bool host_mapped)
 {
     if (n < 1 || n > kMaxN) return BED_ERR_UNSUPPORTED_N;
     if (batch < 0) return BED_ERR_INVALID_ARG;
@@ -174,7 +175,8 @@ bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_
     if (!P) return BED_ERR_INVALID_ARG;
     // TMA bulk staging needs a 16-byte aligned source and a size that is a multiple of 16 bytes for
     // every matrix: A 16-byte aligned and n even.
-    const bool bulk = ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && (n % 2 == 0);
+    // Matrices in mapped host memory are read with plain loads.
+    const bool bulk = !host_mapped && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && (n % 2 == 0);
     const cudaError_t e = launch_eigh(nmax, g, A, W, V, info, batch, *P, kp, counters, bulk, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     return BED_OK;
@@ -257,7 +259,7 @@ void bed_default_params(bed_params* p)
 bed_status bed_eigh_f32(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
                         const bed_params* p, cudaStream_t stream)
 {
-    return bed::eigh_common(A, W, V, info, batch, n, p, nullptr, stream);
+    return bed::eigh_common(A, W, V, info, batch, n, p, nullptr, stream, false);
 }
 
 bed_status bed_eigh_f32_counted(const float* A, float* W, float* V, int32_t* info, int64_t batch,
@@ -265,7 +267,7 @@ bed_status bed_eigh_f32_counted(const float* A, float* W, float* V, int32_t* inf
                                 cudaStream_t stream)
 {
     if (!counters) return BED_ERR_INVALID_ARG;
-    return bed::eigh_common(A, W, V, info, batch, n, p, counters, stream);
+    return bed::eigh_common(A, W, V, info, batch, n, p, counters, stream, false);
 }
 
 bed_status bed_eigh_f32_host(const float* A_host, float* W_host, float* V_host, int32_t* info_host,
@@ -300,7 +302,7 @@ bed_status bed_eigh_f32_host(const float* A_host, float* W_host, float* V_host, 
                                         cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return bed::cuda_fail(e);
         const bed_status st = bed::eigh_common(A_dev + b0 * nn, W_dev + b0 * n, V_dev + b0 * nn,
-                                               info_dev ? info_dev + b0 : nullptr, nb, n, p, nullptr, s);
+                                               info_dev ? info_dev + b0 : nullptr, nb, n, p, nullptr, s, false);
         if (st != BED_OK) return st;
         e = cudaMemcpyAsync(W_host + b0 * n, W_dev + b0 * n, nb * n * sizeof(float), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
@@ -311,6 +313,54 @@ bed_status bed_eigh_f32_host(const float* A_host, float* W_host, float* V_host, 
         if (e != cudaSuccess) return bed::cuda_fail(e);
     }
     return BED_OK;
+}
+
+namespace {
+
+// Device address of the page-locked host range [p, p + bytes) in the current context, or nullptr when
+// any part of it is not page-locked memory mapped into the device's address space. Both ends must lie
+// in the same mapping (their device addresses differ by bytes - 1).
+const void* mapped_range(const void* p, size_t bytes)
+{
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a{}, b{};
+    const void* last = static_cast<const char*>(p) + (bytes - 1);
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();  // clear the error of an unregistered pointer
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    if (static_cast<const char*>(b.devicePointer) - static_cast<const char*>(a.devicePointer) !=
+        static_cast<ptrdiff_t>(bytes - 1))
+        return nullptr;
+    return a.devicePointer;
+}
+
+}  // namespace
+
+bed_status bed_eigh_f32_pinned(const float* A_host, float* W_host, float* V_host, int32_t* info_host,
+                               int64_t batch, int n, const bed_params* p, cudaStream_t stream)
+{
+    if (n < 1 || n > bed::kMaxN) return BED_ERR_UNSUPPORTED_N;
+    if (batch < 0) return BED_ERR_INVALID_ARG;
+    {
+        bed_params prm;
+        bed::KParams kp;
+        if (!bed::make_kparams(p, &prm, &kp)) return BED_ERR_INVALID_ARG;
+    }
+    if (batch == 0) return BED_OK;
+    const size_t nn = static_cast<size_t>(n) * n, b = static_cast<size_t>(batch);
+    const float* A = static_cast<const float*>(mapped_range(A_host, b * nn * sizeof(float)));
+    float* W = static_cast<float*>(const_cast<void*>(mapped_range(W_host, b * n * sizeof(float))));
+    float* V = static_cast<float*>(const_cast<void*>(mapped_range(V_host, b * nn * sizeof(float))));
+    int32_t* info = nullptr;
+    if (info_host) {
+        info = static_cast<int32_t*>(const_cast<void*>(mapped_range(info_host, b * sizeof(int32_t))));
+        if (!info) return BED_ERR_INVALID_ARG;
+    }
+    if (!A || !W || !V) return BED_ERR_INVALID_ARG;
+    return bed::eigh_common(A, W, V, info, batch, n, p, nullptr, stream, true);
 }
 
 bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count,

@@ -6,9 +6,9 @@
 //   a1  Householder tridiagonalization: A in column-owned register tiles, p = tau A v from the
 //       column sums of each warp's block (A is symmetric), one block barrier per reflector
 //   a2  tear the tridiagonal along the static divide tree (Sec. 2.1, Eq. (2)-(3))
-//   a3  2x2 leaves by one Jacobi rotation (Sec. 2.2)
+//   a3  leaves (Sec. 2.2): 1x1; 2x2 by one Jacobi rotation; 3 to 8 rows by implicit QL with Wilkinson shifts
 //   a4  per merge (Eq. (4)-(5)): coupling vector z, pole ordering, deflation
-//   a5  secular roots (Eq. (8)-(21)): G lanes per root, hybrid-section then Halley in coordinates
+//   a5  secular roots (Eq. (8)-(21)): one lane per root, hybrid-section then Halley in coordinates
 //       relative to the nearer pole; a warp stops iterating when all of its lanes have converged
 //       (the GPU form of the progressive batch shrinkage, Eq. (22))
 //   a6  Gu-Eisenstat z-hat (Eq. (25)) and normalized eigenvectors (Eq. (24))
@@ -17,8 +17,8 @@
 //       column of Q held in the registers of its G lanes
 //   a9  ascending order, sign convention, store
 // Thread layouts (NT = NMAX * G threads): "position" pos = tid / G, sub = tid % G: G consecutive
-// lanes share one row / column / root and combine their partial results with shuffles inside the
-// group; a1 and a7 use their own register tilings, described where they run.
+// lanes share one row / column and combine their partial results with shuffles inside the group;
+// a1 and a7 use their own register tilings and a5 one lane per root, described where they run.
 #pragma once
 
 #include <atomic>
@@ -625,7 +625,19 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         }
         phase ^= 1u;
     } else {
-        for (int i = tid; i < n * n; i += NT) S.M[i] = __ldg(Ab + i);
+        // all loads of a thread in flight at once: the source may be host memory across the link
+        constexpr int PER = NMAX / G;  // NMAX^2 / NT
+        float r[PER];
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int i = tid + t * NT;
+            r[t] = (i < n * n) ? Ab[i] : 0.f;
+        }
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int i = tid + t * NT;
+            if (i < n * n) S.M[i] = r[t];
+        }
     }
     if (timed_out) atomicOr(&S.info, BED_INFO_TIMEOUT);
     team_sync<NT>(bar_id);
@@ -1036,32 +1048,38 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             compact();
             team_sync<NT>(bar_id);
         }
-        // P5: secular roots, G lanes per root
-        {
-            int K = 0, q = 0;
+        // P5: secular roots, one lane per root: root t is solved by thread t. Every root repeats the
+        // same scalar step logic around its pole sums, so splitting a root's sums over several lanes
+        // would repeat that logic on each of them; one lane per root issues the fewest instructions.
+        constexpr int GS = 1;  // lanes per root
+        if (warp * (32 / GS) < n) {  // warps holding no root skip the phase (the vote inside is per warp)
+            const int t = tid / GS;
+            const int bt = (t < n) ? plan.blk[L][t] : 0xFF;
+            int K = 0, q = 0, lot = 0, hit = 0;
             float sc = 1.f, rho = 0.f;
-            if (act) {
-                K = S.bK[lb];
-                q = pos - lo;
-                sc = S.bsc[lb];
-                rho = S.brho[lb] * sc;
+            if (bt != 0xFF) {
+                const int lbt = bt - l0;
+                lot = plan.m_lo[bt];
+                hit = plan.m_hi[bt];
+                K = S.bK[lbt];
+                q = t - lot;
+                sc = S.bsc[lbt];
+                rho = S.brho[lbt] * sc;
             }
-            const bool part = act && (q < K);
-            if (act && q == 0 && sub == 0) atomicAdd(&S.deflated, static_cast<unsigned>(hi - lo - K));
-            const RootOut r = secular_root<G>(S.cdz + lo, K, q, rho, kp, part, sub);
-            if (sub == 0) {
-                if (part) {
-                    S.org[lo + q] = lo + r.org;
-                    S.tq[lo + q] = r.tau;
-                    S.lam[lo + q] = (S.cdz[lo + r.org].x + r.tau) * (1.f / sc);
-                    atomicAdd(&S.evals, static_cast<unsigned>(r.evals));
-                    atomicAdd(&S.roots, 1u);
-                    if (!r.conv) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
-                } else if (act) {
-                    S.org[lo + q] = lo + q;
-                    S.tq[lo + q] = 0.f;
-                    S.lam[lo + q] = S.cdz[lo + q].x * (1.f / sc);
-                }
+            const bool part = (bt != 0xFF) && (q < K);
+            if (bt != 0xFF && q == 0 && tid % GS == 0) atomicAdd(&S.deflated, static_cast<unsigned>(hit - lot - K));
+            const RootOut r = secular_root<GS>(S.cdz + lot, K, q, rho, kp, part, tid % GS);
+            if (part && tid % GS == 0) {
+                S.org[t] = lot + r.org;
+                S.tq[t] = r.tau;
+                S.lam[t] = (S.cdz[lot + r.org].x + r.tau) * (1.f / sc);
+                atomicAdd(&S.evals, static_cast<unsigned>(r.evals));
+                atomicAdd(&S.roots, 1u);
+                if (!r.conv) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
+            } else if (bt != 0xFF && tid % GS == 0) {
+                S.org[t] = t;
+                S.tq[t] = 0.f;
+                S.lam[t] = S.cdz[t].x * (1.f / sc);
             }
         }
         team_sync<NT>(bar_id);
@@ -1210,23 +1228,23 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
 
     // ---------------- a8: back-transform V = H_0 ... H_{n-3} Q_T ----------------------------
     // Blocks of kBT reflectors: H_{k0} ... H_{k0+b-1} = I - Y T Y^T with T upper triangular
-    // (forward accumulation); column r of Y is v_{k0+r}, zero above its unit entry. Blocks are applied
-    // last to first, Q <- Q - Y (T (Y^T Q)), with column pos of Q held in registers by its G lanes
-    // (rows sub + G t): Y^T Q is a sum over those lanes, so no barrier separates the blocks.
+    // (forward accumulation); column r of Y is v_{k0+r}, zero above its unit entry. Each block is
+    // stored once more as W = Y T, so that applying it is two passes over the rows,
+    // Q <- Q - W (Y^T Q). Blocks are applied last to first, with column pos of Q held in registers by
+    // its G lanes (rows sub + G t): Y^T Q is a sum over those lanes, so no barrier separates the blocks.
     if (n >= 3) {
         const int nr = n - 2;
         const int ngr = (nr + kBT - 1) / kBT;
         const float* Yt = S.A;
-        float* Tm = S.M;  // ngr blocks of kBT x kBT, row-major; zero below the diagonal
+        float* Wt = S.M;  // W, in the layout of Yt (the merges are done with M)
+        static_assert(kBT == 8, "two 16-byte reads per row of a block");
         for (int g = warp; g < ngr; g += NW) {
             const int k0 = g * kBT;
             const int bsz = min(kBT, nr - k0);
-            float* T = Tm + g * kBT * kBT;
-            for (int e = lane; e < kBT * kBT; e += 32) T[e] = 0.f;
-            __syncwarp();
             // Gram entries Y[:, r]^T Y[:, j], r < j (28 pairs, r-major): every lane forms the products
             // of its rows (two 16-byte reads per row), then a halving exchange over the 32 lanes
-            // leaves pair `lane` summed on lane `lane`; stored at T[j][r]
+            // leaves pair `lane` summed on lane `lane`
+            float gram;
             {
                 float v[32];
 #pragma unroll
@@ -1258,45 +1276,48 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                         v[t] = keep + __shfl_xor_sync(kFull, send, o);
                     }
                 }
-                int p = lane, r = 0;
-                while (r < kBT - 1 && p >= kBT - 1 - r) {
-                    p -= kBT - 1 - r;
-                    ++r;
-                }
-                const int j = r + 1 + p;
-                if (r < kBT - 1 && j < bsz) T[j * kBT + r] = v[0];
+                gram = v[0];
             }
-            __syncwarp();
             // T[jj][jj] = tau_jj; T[0:jj, jj] = -tau_jj T[0:jj, 0:jj] Gram[0:jj, jj]: lane r keeps row r
-            // of T in registers and reads only its own earlier entries and the Gram column
-            {
-                float trow[kBT];
+            // of T in registers; Gram(s, jj) is pair s (15 - s) / 2 + jj - s - 1, read from its lane
+            float trow[kBT];
 #pragma unroll
-                for (int t = 0; t < kBT; ++t) trow[t] = 0.f;
-                for (int jj = 0; jj < bsz; ++jj) {
-                    const float tj = S.tau[k0 + jj];
+            for (int t = 0; t < kBT; ++t) trow[t] = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < kBT; ++jj) {
+                float acc = 0.f;
+#pragma unroll
+                for (int s2 = 0; s2 < jj; ++s2)
+                    acc = fmaf(trow[s2], __shfl_sync(kFull, gram, s2 * (15 - s2) / 2 + jj - s2 - 1), acc);
+                const float tj = (jj < bsz) ? S.tau[k0 + jj] : 0.f;
+                trow[jj] = (lane < jj) ? -tj * acc : ((lane == jj) ? tj : 0.f);
+            }
+            // W = Y T for this lane's rows; T[r][c] (r <= c) comes from lane r
+#pragma unroll
+            for (int m = 0; m < (NMAX + 31) / 32; ++m) {
+                const int i = lane + 32 * m;
+                float y[kBT] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (i < NMAX) {
+                    const float4 ya = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0));
+                    const float4 yb = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0 + 4));
+                    y[0] = ya.x, y[1] = ya.y, y[2] = ya.z, y[3] = ya.w;
+                    y[4] = yb.x, y[5] = yb.y, y[6] = yb.z, y[7] = yb.w;
+                }
+                float w[kBT];
+#pragma unroll
+                for (int c = 0; c < kBT; ++c) {
                     float acc = 0.f;
 #pragma unroll
-                    for (int s2 = 0; s2 < kBT; ++s2)
-                        if (s2 < jj) acc = fmaf(trow[s2], T[jj * kBT + s2], acc);
-                    const float val = (lane < jj) ? -tj * acc : ((lane == jj) ? tj : 0.f);
-#pragma unroll
-                    for (int s2 = 0; s2 < kBT; ++s2)
-                        if (s2 == jj) trow[s2] = val;
+                    for (int r = 0; r <= c; ++r) acc = fmaf(y[r], __shfl_sync(kFull, trow[c], r), acc);
+                    w[c] = acc;
                 }
-                __syncwarp();
-                if (lane < kBT) {
-#pragma unroll
-                    for (int s2 = 0; s2 < kBT; ++s2)
-                        if (s2 >= lane) T[lane * kBT + s2] = trow[s2];
+                if (i < NMAX) {
+                    *reinterpret_cast<float4*>(Wt + yt_index<NMAX>(i, k0)) = make_float4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<float4*>(Wt + yt_index<NMAX>(i, k0 + 4)) = make_float4(w[4], w[5], w[6], w[7]);
                 }
             }
-            __syncwarp();
-            for (int e = lane; e < kBT * kBT; e += 32)
-                if (e % kBT < e / kBT) T[e] = 0.f;
         }
         team_sync<NT>(bar_id);
-        static_assert(kBT == 8, "two 16-byte reads per row of a block");
         constexpr int RPT = NMAX / G;
         float q[RPT];
 #pragma unroll
@@ -1306,8 +1327,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         }
         for (int g = ngr - 1; g >= 0; --g) {
             const int k0 = g * kBT;
-            const float* T = Tm + g * kBT * kBT;
-            // W1 = Y^T q over this lane's rows; rows up to k0 are zero in every column of Y
+            // W1 = Y^T q over this lane's rows; rows up to k0 are zero in every column of Y and W
             float w1[kBT];
 #pragma unroll
             for (int r = 0; r < kBT; ++r) w1[r] = 0.f;
@@ -1328,37 +1348,22 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             }
 #pragma unroll
             for (int r = 0; r < kBT; ++r) w1[r] = gsum<G>(w1[r]);
-            // W2 = T W1
-            float w2[kBT];
-#pragma unroll
-            for (int r = 0; r < kBT; ++r) {
-                const float4 ta = *reinterpret_cast<const float4*>(T + r * kBT);
-                const float4 tb = *reinterpret_cast<const float4*>(T + r * kBT + 4);
-                float sacc = ta.x * w1[0];
-                sacc = fmaf(ta.y, w1[1], sacc);
-                sacc = fmaf(ta.z, w1[2], sacc);
-                sacc = fmaf(ta.w, w1[3], sacc);
-                sacc = fmaf(tb.x, w1[4], sacc);
-                sacc = fmaf(tb.y, w1[5], sacc);
-                sacc = fmaf(tb.z, w1[6], sacc);
-                w2[r] = fmaf(tb.w, w1[7], sacc);
-            }
-            // q -= Y W2
+            // q -= W W1
 #pragma unroll
             for (int t = 0; t < RPT; ++t) {
                 if (G * t + G - 1 <= k0) continue;
                 const int i = sub + G * t;
-                const float4 ya = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0));
-                const float4 yb = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0 + 4));
+                const float4 wa = *reinterpret_cast<const float4*>(Wt + yt_index<NMAX>(i, k0));
+                const float4 wb = *reinterpret_cast<const float4*>(Wt + yt_index<NMAX>(i, k0 + 4));
                 float v = q[t];
-                v = fmaf(-ya.x, w2[0], v);
-                v = fmaf(-ya.y, w2[1], v);
-                v = fmaf(-ya.z, w2[2], v);
-                v = fmaf(-ya.w, w2[3], v);
-                v = fmaf(-yb.x, w2[4], v);
-                v = fmaf(-yb.y, w2[5], v);
-                v = fmaf(-yb.z, w2[6], v);
-                q[t] = fmaf(-yb.w, w2[7], v);
+                v = fmaf(-wa.x, w1[0], v);
+                v = fmaf(-wa.y, w1[1], v);
+                v = fmaf(-wa.z, w1[2], v);
+                v = fmaf(-wa.w, w1[3], v);
+                v = fmaf(-wb.x, w1[4], v);
+                v = fmaf(-wb.y, w1[5], v);
+                v = fmaf(-wb.z, w1[6], v);
+                q[t] = fmaf(-wb.w, w1[7], v);
             }
         }
 #pragma unroll

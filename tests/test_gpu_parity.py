@@ -281,6 +281,56 @@ def test_host_entry_point_pipelined(chunks):
                                Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), None, 0, 0, 0) == B.BED_ERR_UNSUPPORTED_N
 
 
+@pytest.mark.parametrize("n,b", [(1, 3), (5, 70), (37, 300), (64, 513)])
+def test_pinned_zero_copy_entry_point(n, b):
+    """bed_eigh_f32_pinned (the kernel reads and writes page-locked host memory directly) gives the
+    results of bed_eigh_f32 on device buffers, bitwise."""
+    A = wl.covariance(b, n, seed=78 + n)
+    Ah = torch.from_numpy(A).pin_memory()
+    Wh = torch.full((b, n), -7.0).pin_memory()
+    Vh = torch.full((b, n, n), -7.0).pin_memory()
+    Ih = torch.full((b,), -1, dtype=torch.int32).pin_memory()
+    s = torch.cuda.Stream()
+    assert B.bed_eigh_f32_pinned(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, None,
+                                 s.cuda_stream) == B.BED_OK
+    s.synchronize()
+    W, V, info = run_gpu(A)
+    assert np.array_equal(Wh.numpy(), W) and np.array_equal(Vh.numpy(), V) and np.array_equal(Ih.numpy(), info)
+    if n == 64:
+        Wo, Vo = run_oracle(A[:40])
+        assert_parity(A[:40], Wh.numpy()[:40], Vh.numpy()[:40], Ih.numpy()[:40], Wo, Vo, "pinned entry point")
+
+
+def test_pinned_entry_point_rejects_unmapped_buffers():
+    """Pageable host memory and device memory are refused before anything is enqueued."""
+    b, n = 4, 8
+    Ah = torch.from_numpy(wl.covariance(b, n, seed=5)).pin_memory()
+    Wh = torch.empty(b, n).pin_memory()
+    Vh = torch.empty(b, n, n).pin_memory()
+    pageable = np.zeros((b, n, n), dtype=np.float32)
+    Vd = torch.empty(b, n, n, device="cuda")
+    ok = (Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr())
+    assert B.bed_eigh_f32_pinned(pageable.ctypes.data, ok[1], ok[2], None, b, n) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32_pinned(ok[0], ok[1], pageable.ctypes.data, None, b, n) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32_pinned(ok[0], ok[1], Vd.data_ptr(), None, b, n) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32_pinned(ok[0], ok[1], ok[2], pageable.ctypes.data, b, n) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32_pinned(ok[0], ok[1], ok[2], None, b, 65) == B.BED_ERR_UNSUPPORTED_N
+    assert B.bed_eigh_f32_pinned(0, 0, 0, None, 0, n) == B.BED_OK
+    assert B.bed_eigh_f32_pinned(ok[0], ok[1], ok[2], None, b, n) == B.BED_OK
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("chunks", [0, 2])
+def test_many_batches_host_copy_path(chunks):
+    """batched_eigh_many on host tensors through the copy-engine entry point (host_chunks > 0) agrees
+    bitwise with the zero-copy default."""
+    mats = [torch.from_numpy(wl.covariance(33, n, seed=90 + n)) for n in (64, 9, 40)]
+    a = B.batched_eigh_many(mats, return_info=True)
+    c = B.batched_eigh_many(mats, return_info=True, host_chunks=max(chunks, 1))
+    for (W, V, i), (W2, V2, i2) in zip(a, c):
+        assert torch.equal(W, W2) and torch.equal(V, V2) and torch.equal(i, i2)
+
+
 @pytest.mark.parametrize("n", [5, 16, 40, 64])
 def test_power_of_two_scaling_is_exact(n):
     """The kernel scales every matrix by a power of two before solving and back after: A 2^e gives
