@@ -148,6 +148,25 @@ bed_status bed_eigh_f32_pinned(const float* A_host, float* W_host, float* V_host
                                int64_t batch, int n, const bed_params* p, cudaStream_t stream);
 
 /*
+ * Several uniform batches of different n in page-locked host memory, solved by one call (the
+ * zero-copy path of bed_eigh_f32_pinned for each batch, with the stream fork and join done here).
+ *   count            number of batches (0: nothing is enqueued)
+ *   ns[k], batches[k] size and matrix count of batch k (a batch of 0 matrices is skipped)
+ *   A_host[k], W_host[k], V_host[k], info_host[k]  its buffers, as in bed_eigh_f32_pinned; info_host
+ *                    may be NULL (no info for any batch) or hold NULL entries
+ *   origin           the batches start after the work already enqueued on `origin`, and `origin` waits
+ *                    for all of them (through two events the library keeps per calling thread)
+ *   side, nside      streams the launches run on, largest n first, batch j of that order on
+ *                    side[j % nside], so that batches of different n run side by side
+ * Every argument of every batch is checked before anything is enqueued (BED_ERR_UNSUPPORTED_N,
+ * BED_ERR_INVALID_ARG); a CUDA error (BED_ERR_CUDA) may leave earlier launches of the call enqueued.
+ * The results are in host memory once `origin` has reached this call's work.
+ */
+bed_status bed_eigh_many_f32_pinned(int count, const int* ns, const int64_t* batches, const float* const* A_host,
+                                    float* const* W_host, float* const* V_host, int32_t* const* info_host,
+                                    const bed_params* p, cudaStream_t origin, const cudaStream_t* side, int nside);
+
+/*
  * Ragged batches: matrices of mixed size in one persistent launch (Sec. 2.1 notes that dividing turns a
  * batch of B matrices into B*R blocks; here blocks of all sizes share the GPU in one launch).
  *

@@ -7,7 +7,8 @@ needed) on first use.
 
 
 def __getattr__(name):
-    if name in ("batched_eigh", "batched_eigh_many", "batched_eigh_ragged", "eigh", "make_params", "BedError"):
+    if name in ("batched_eigh", "batched_eigh_many", "batched_eigh_many_async", "batched_eigh_ragged", "eigh",
+                "make_params", "BedError"):
         from . import binding
 
         return getattr(binding, name)

@@ -73,6 +73,7 @@ EXPORTED = [
     "bed_eigh_f32_counted",
     "bed_eigh_f32_host",
     "bed_eigh_f32_pinned",
+    "bed_eigh_many_f32_pinned",
     "bed_eigh_backward_f32",
     "bed_eigh_ragged_f32",
     "bed_eigh_ragged_f32_noalloc",
@@ -114,6 +115,9 @@ def lib() -> C.CDLL:
             L.bed_eigh_f32_host.restype = C.c_int
             L.bed_eigh_f32_pinned.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.POINTER(bed_params), vp]
             L.bed_eigh_f32_pinned.restype = C.c_int
+            L.bed_eigh_many_f32_pinned.argtypes = [C.c_int, vp, vp, vp, vp, vp, vp, C.POINTER(bed_params), vp, vp,
+                                                   C.c_int]
+            L.bed_eigh_many_f32_pinned.restype = C.c_int
             L.bed_max_n.argtypes = []
             L.bed_max_n.restype = C.c_int
             L.bed_status_string.argtypes = [C.c_int]
@@ -175,6 +179,17 @@ def bed_eigh_f32_pinned(A_host: int, W_host: int, V_host: int, info_host: int | 
                         params: bed_params | None = None, stream: int = 0) -> int:
     return lib().bed_eigh_f32_pinned(A_host, W_host, V_host, info_host, batch, n,
                                      C.byref(params) if params is not None else None, stream)
+
+
+def bed_eigh_many_f32_pinned(ns, batches, A_host, W_host, V_host, info_host, params: bed_params | None,
+                             origin: int, side) -> int:
+    """Sequences of sizes, counts and host pointers (ints; info_host None or a sequence with None entries)."""
+    k = len(ns)
+    P = C.c_void_p * k
+    infos = None if info_host is None else P(*[p or None for p in info_host])
+    return lib().bed_eigh_many_f32_pinned(k, (C.c_int * k)(*ns), (C.c_int64 * k)(*batches), P(*A_host), P(*W_host),
+                                          P(*V_host), infos, C.byref(params) if params is not None else None, origin,
+                                          (C.c_void_p * len(side))(*side), len(side))
 
 
 def bed_eigh_f32_host(A_host: int, W_host: int, V_host: int, info_host: int | None, batch: int, n: int,
@@ -482,10 +497,11 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
 
     Each batch gets one launch on its own stream, forked from the current stream and joined back to it,
     so that batches of different n run side by side on the GPU instead of one after another. CPU tensors
-    are solved in place in page-locked host memory (``bed_eigh_f32_pinned``: the kernel reads the
-    matrices and writes the results across the host-device link, no device buffers); with
-    ``host_chunks > 0`` they go through ``bed_eigh_f32_host`` instead (copy in, solve and copy out in that
-    many pieces over two streams). Host results are returned once they are in (page-locked) host memory.
+    are solved in place in page-locked host memory (``bed_eigh_many_f32_pinned``: the kernels read the
+    matrices and write the results across the host-device link, no device buffers, one call for all
+    batches); with ``host_chunks > 0`` they go through ``bed_eigh_f32_host`` instead (copy in, solve and
+    copy out in that many pieces over two streams). Host results are returned once they are in
+    (page-locked) host memory.
     Returns a list of ``(W, V)`` (``(W, V, info)`` with ``return_info``), in the order of ``mats``."""
     mats = list(mats)
     if not mats:
@@ -499,53 +515,39 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
     if not host and any(M.device != dev for M in mats):
         raise ValueError("batched_eigh_many expects all batches on one CUDA device")
     cur = torch.cuda.current_stream(dev)
+    if host and host_chunks <= 0:
+        return _many_pinned(mats, params, check, return_info, dev, cur)
     fork = torch.cuda.Event()
     fork.record(cur)
     # largest n first: its launch is the longest and should start first
     order = sorted(range(len(mats)), key=lambda i: -mats[i].shape[-1])
     outs = [None] * len(mats)
-    copies = host and host_chunks > 0
-    side = _streams(dev, 2 * len(mats) if copies else len(mats))
-    keep = []  # device scratch of the copy path, alive until the final synchronize
+    side = _streams(dev, 2 * len(mats) if host else len(mats))
+    keep = []  # host inputs and device scratch of the copy path, alive until the final synchronize
     for k, i in enumerate(order):
         if host:
-            A = mats[i]
-            if A.dtype != torch.float32 or A.dim() < 2 or A.shape[-1] != A.shape[-2]:
-                raise ValueError("batched_eigh_many expects float32 [..., n, n] batches")
-            lead, n = A.shape[:-2], A.shape[-1]
-            Ah = A.reshape(-1, n, n).contiguous()
-            if not Ah.is_pinned():
-                Ah = Ah.pin_memory()
+            Ah, lead, n = _host_batch(mats[i])
             b = Ah.shape[0]
             Wh = torch.empty((b, n), dtype=torch.float32, pin_memory=True)
             Vh = torch.empty((b, n, n), dtype=torch.float32, pin_memory=True)
             Ih = torch.empty((b,), dtype=torch.int32, pin_memory=True)
             outs[i] = (Wh, Vh, Ih, True, lead, n)
-            keep.append(Ah)
-            if copies:
-                # copy-in / solve / copy-out pipelined in pieces over two streams (bed_eigh_f32_host)
-                s0, s1 = side[2 * k], side[2 * k + 1]
-                s0.wait_event(fork)
-                s1.wait_event(fork)
-                with torch.cuda.stream(s0):
-                    Ad = torch.empty((b, n, n), dtype=torch.float32, device=dev)
-                    Wd = torch.empty((b, n), dtype=torch.float32, device=dev)
-                    Vd = torch.empty((b, n, n), dtype=torch.float32, device=dev)
-                    Id = torch.empty((b,), dtype=torch.int32, device=dev)
-                for t in (Ad, Wd, Vd, Id):
-                    t.record_stream(s1)
-                keep.append((Ad, Wd, Vd, Id))
-                _check(bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, params,
-                                         Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), Id.data_ptr(), host_chunks,
-                                         s0.cuda_stream, s1.cuda_stream))
-                used = (s0, s1)
-            else:
-                s = side[k]
-                s.wait_event(fork)
-                _check(bed_eigh_f32_pinned(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, params,
-                                           s.cuda_stream))
-                used = (s,)
-            for s in used:
+            # copy-in / solve / copy-out pipelined in pieces over two streams (bed_eigh_f32_host)
+            s0, s1 = side[2 * k], side[2 * k + 1]
+            s0.wait_event(fork)
+            s1.wait_event(fork)
+            with torch.cuda.stream(s0):
+                Ad = torch.empty((b, n, n), dtype=torch.float32, device=dev)
+                Wd = torch.empty((b, n), dtype=torch.float32, device=dev)
+                Vd = torch.empty((b, n, n), dtype=torch.float32, device=dev)
+                Id = torch.empty((b,), dtype=torch.int32, device=dev)
+            for t in (Ad, Wd, Vd, Id):
+                t.record_stream(s1)
+            keep.append((Ah, Ad, Wd, Vd, Id))
+            _check(bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, params,
+                                     Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), Id.data_ptr(), host_chunks,
+                                     s0.cuda_stream, s1.cuda_stream))
+            for s in (s0, s1):
                 join = torch.cuda.Event()
                 join.record(s)
                 cur.wait_event(join)
@@ -563,6 +565,94 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
         cur.synchronize()
         del keep
     return [_eigh_finish(o, check, return_info) for o in outs]
+
+
+def _host_batch(A: torch.Tensor):
+    """A CPU batch as a page-locked [b, n, n] tensor, with its leading shape and n."""
+    if A.dtype != torch.float32 or A.dim() < 2 or A.shape[-1] != A.shape[-2]:
+        raise ValueError("batched_eigh_many expects float32 [..., n, n] batches")
+    lead, n = A.shape[:-2], A.shape[-1]
+    Ah = A.reshape(-1, n, n).contiguous()
+    if not Ah.is_pinned():
+        Ah = Ah.pin_memory()
+    return Ah, lead, n
+
+
+def _many_pinned(mats, params, check, return_info, dev, cur):
+    """Host batches through one bed_eigh_many_f32_pinned call on the current stream, then wait."""
+    pend = _enqueue_pinned(mats, params, dev, cur, _streams(dev, len(mats)))
+    return pend.wait(check, return_info)
+
+
+class PendingEigh:
+    """Results of an enqueued host-memory solve: :meth:`wait` blocks until they are in (page-locked)
+    host memory and returns them like :func:`batched_eigh_many`. Dropping an unfinished one waits."""
+
+    def __init__(self, outs, stream, keep):
+        self._outs, self._stream, self._keep = outs, stream, keep
+
+    def done(self) -> bool:
+        return self._stream.query()
+
+    def wait(self, check: bool = False, return_info: bool = False):
+        self._stream.synchronize()
+        self._keep = None
+        return [_eigh_finish(o, check, return_info) for o in self._outs]
+
+    def __del__(self):
+        if getattr(self, "_keep", None) is not None:
+            try:
+                self._stream.synchronize()
+            except Exception:
+                pass
+
+
+def _enqueue_pinned(mats, params, dev, origin, side):
+    ins = [_host_batch(M) for M in mats]
+    outs = []
+    for Ah, lead, n in ins:
+        b = Ah.shape[0]
+        W = torch.empty((b, n), dtype=torch.float32, pin_memory=True)
+        V = torch.empty((b, n, n), dtype=torch.float32, pin_memory=True)
+        I = torch.empty((b,), dtype=torch.int32, pin_memory=True)
+        outs.append((W, V, I, True, lead, n))
+    live = [k for k, (Ah, _, _) in enumerate(ins) if Ah.shape[0] > 0]
+    if live:
+        _check(bed_eigh_many_f32_pinned([ins[k][2] for k in live], [ins[k][0].shape[0] for k in live],
+                                        [ins[k][0].data_ptr() for k in live], [outs[k][0].data_ptr() for k in live],
+                                        [outs[k][1].data_ptr() for k in live], [outs[k][2].data_ptr() for k in live],
+                                        params, origin.cuda_stream, [s.cuda_stream for s in side[: len(live)]]))
+    return PendingEigh(outs, origin, [x[0] for x in ins])
+
+
+_async_slots: dict = {}
+
+
+def batched_eigh_many_async(mats, params: bed_params | None = None, slots: int = 2) -> PendingEigh:
+    """Enqueues the zero-copy solve of several uniform batches held in CPU tensors and returns at once.
+
+    Calls rotate over ``slots`` sets of streams (a completion stream and one stream per batch), so that
+    up to ``slots`` calls are in flight and one call's reads and writes across the host-device link
+    overlap another's solve. The work does not wait for anything on the caller's current stream (the
+    inputs are host tensors). Returns a :class:`PendingEigh`; its ``wait()`` gives the results."""
+    mats = list(mats)
+    if not torch.cuda.is_available():
+        raise BedError("batched_eigh_many_async needs a CUDA device; there is no CPU path")
+    if any(M.is_cuda for M in mats):
+        raise ValueError("batched_eigh_many_async expects CPU tensors")
+    if slots < 1:
+        raise ValueError("slots must be >= 1")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = _async_slots.setdefault(dev.index, {"next": 0, "sets": []})
+    sets = st["sets"]
+    k = st["next"] % slots
+    st["next"] = k + 1
+    while len(sets) <= k:
+        sets.append([torch.cuda.Stream(dev)])
+    streams = sets[k]
+    while len(streams) < 1 + len(mats):
+        streams.append(torch.cuda.Stream(dev))
+    return _enqueue_pinned(mats, params, dev, streams[0], streams[1:])
 
 
 def batched_eigh_ragged(mats, params: bed_params | None = None, tuning: bed_ragged_tuning | None = None,

@@ -1,4 +1,5 @@
 // C ABI of the batched eigensolver: argument validation, the divide-tree plan, launch selection.
+#include <algorithm>
 #include <cfloat>
 #include <cstddef>
 #include <cstdio>
@@ -139,16 +140,10 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
     return true;
 }
 
-bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
-                       const bed_params* p, bed_counters* counters, cudaStream_t stream, bool host_mapped)
+// Team shape: nmax rows of tiles, G lanes per row; the smallest nmax that holds n unless the caller
+// asks for a thread count, which then selects the smallest (nmax >= n, G) with G * nmax equal to it.
+bool team_shape(int n, const bed_params& prm, int* nmax_out, int* g_out)
 {
-    if (n < 1 || n > kMaxN) return BED_ERR_UNSUPPORTED_N;
-    if (batch < 0) return BED_ERR_INVALID_ARG;
-    bed_params prm;
-    KParams kp;
-    if (!make_kparams(p, &prm, &kp)) return BED_ERR_INVALID_ARG;
-    // team shape: nmax rows of tiles, G lanes per row; the smallest nmax that holds n unless the caller
-    // asks for a thread count, which then selects the smallest (nmax >= n, G) with G * nmax equal to it
     int nmax = n <= 16 ? 16 : (n <= 32 ? 32 : (n <= 48 ? 48 : 64));
     int g = 4;
     if (prm.threads_per_matrix != 0) {
@@ -162,8 +157,23 @@ bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_
                     found = true;
                 }
         }
-        if (!found) return BED_ERR_INVALID_ARG;
+        if (!found) return false;
     }
+    *nmax_out = nmax;
+    *g_out = g;
+    return true;
+}
+
+bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
+                       const bed_params* p, bed_counters* counters, cudaStream_t stream, bool host_mapped)
+{
+    if (n < 1 || n > kMaxN) return BED_ERR_UNSUPPORTED_N;
+    if (batch < 0) return BED_ERR_INVALID_ARG;
+    bed_params prm;
+    KParams kp;
+    if (!make_kparams(p, &prm, &kp)) return BED_ERR_INVALID_ARG;
+    int nmax = 0, g = 0;
+    if (!team_shape(n, prm, &nmax, &g)) return BED_ERR_INVALID_ARG;
     if (batch == 0) return BED_OK;
     if (!A || !W || !V) return BED_ERR_INVALID_ARG;
     const uintptr_t mis = (reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(W) |
@@ -361,6 +371,90 @@ bed_status bed_eigh_f32_pinned(const float* A_host, float* W_host, float* V_host
     }
     if (!A || !W || !V) return BED_ERR_INVALID_ARG;
     return bed::eigh_common(A, W, V, info, batch, n, p, nullptr, stream, true);
+}
+
+bed_status bed_eigh_many_f32_pinned(int count, const int* ns, const int64_t* batches, const float* const* A_host,
+                                    float* const* W_host, float* const* V_host, int32_t* const* info_host,
+                                    const bed_params* p, cudaStream_t origin, const cudaStream_t* side, int nside)
+{
+    if (count < 0 || (count > 0 && (!ns || !batches || !A_host || !W_host || !V_host || !side || nside < 1)))
+        return BED_ERR_INVALID_ARG;
+    bed_params prm;
+    {
+        bed::KParams kp;
+        if (!bed::make_kparams(p, &prm, &kp)) return BED_ERR_INVALID_ARG;
+    }
+    // validate every batch (and translate its buffers to device addresses) before anything is enqueued
+    struct Dev {
+        const float* A;
+        float *W, *V;
+        int32_t* info;
+    };
+    std::vector<Dev> dp(count);
+    std::vector<int> order;
+    for (int k = 0; k < count; ++k) {
+        const int n = ns[k];
+        if (n < 1 || n > bed::kMaxN) return BED_ERR_UNSUPPORTED_N;
+        int nmax = 0, g = 0;
+        if (batches[k] < 0 || !bed::team_shape(n, prm, &nmax, &g)) return BED_ERR_INVALID_ARG;
+        if (batches[k] == 0) continue;
+        const size_t nn = static_cast<size_t>(n) * n, b = static_cast<size_t>(batches[k]);
+        Dev& d = dp[k];
+        d.A = static_cast<const float*>(mapped_range(A_host[k], b * nn * sizeof(float)));
+        d.W = static_cast<float*>(const_cast<void*>(mapped_range(W_host[k], b * n * sizeof(float))));
+        d.V = static_cast<float*>(const_cast<void*>(mapped_range(V_host[k], b * nn * sizeof(float))));
+        d.info = nullptr;
+        if (info_host && info_host[k]) {
+            d.info = static_cast<int32_t*>(const_cast<void*>(mapped_range(info_host[k], b * sizeof(int32_t))));
+            if (!d.info) return BED_ERR_INVALID_ARG;
+        }
+        if (!d.A || !d.W || !d.V || d.A == d.V) return BED_ERR_INVALID_ARG;
+        order.push_back(k);
+    }
+    if (order.empty()) return BED_OK;
+    // largest n first: its launch is the longest
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ns[a] > ns[b]; });
+    // fork from and join back to `origin` through two events of this thread (one record / wait pair at a
+    // time, so that reusing them is safe)
+    struct Events {
+        int dev = -1;
+        cudaEvent_t fork = nullptr, join = nullptr;
+    };
+    thread_local std::vector<Events> evs;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return bed::cuda_fail(e);
+    Events* ev = nullptr;
+    for (auto& x : evs)
+        if (x.dev == dev) ev = &x;
+    if (!ev) {
+        Events x;
+        x.dev = dev;
+        e = cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return bed::cuda_fail(e);
+        evs.push_back(x);
+        ev = &evs.back();
+    }
+    e = cudaEventRecord(ev->fork, origin);
+    if (e != cudaSuccess) return bed::cuda_fail(e);
+    const int used = nside < static_cast<int>(order.size()) ? nside : static_cast<int>(order.size());
+    for (int s = 0; s < used; ++s) {
+        e = cudaStreamWaitEvent(side[s], ev->fork, 0);
+        if (e != cudaSuccess) return bed::cuda_fail(e);
+    }
+    for (size_t j = 0; j < order.size(); ++j) {
+        const int k = order[j];
+        const bed_status st = bed::eigh_common(dp[k].A, dp[k].W, dp[k].V, dp[k].info, batches[k], ns[k], p, nullptr,
+                                               side[j % used], true);
+        if (st != BED_OK) return st;
+    }
+    for (int s = 0; s < used; ++s) {
+        e = cudaEventRecord(ev->join, side[s]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, ev->join, 0);
+        if (e != cudaSuccess) return bed::cuda_fail(e);
+    }
+    return BED_OK;
 }
 
 bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count,

@@ -320,6 +320,56 @@ def test_pinned_entry_point_rejects_unmapped_buffers():
     torch.cuda.synchronize()
 
 
+def test_many_pinned_entry_point():
+    """bed_eigh_many_f32_pinned: several sizes (one of them empty) in one call agree bitwise with the
+    device path; a bad buffer in any batch is refused before anything is enqueued."""
+    ns, bs = [7, 64, 30, 12], [21, 40, 0, 9]
+    A = [torch.from_numpy(wl.covariance(max(b, 1), n, seed=700 + n))[:b].contiguous().pin_memory()
+         for n, b in zip(ns, bs)]
+    W = [torch.full((b, n), -7.0).pin_memory() for n, b in zip(ns, bs)]
+    V = [torch.full((b, n, n), -7.0).pin_memory() for n, b in zip(ns, bs)]
+    I = [torch.full((b,), -1, dtype=torch.int32).pin_memory() for b in bs]
+    side = [torch.cuda.Stream() for _ in range(2)]
+    cur = torch.cuda.current_stream()
+    args = lambda Wp: ([t.data_ptr() for t in A], Wp, [t.data_ptr() for t in V], [t.data_ptr() for t in I])
+    pageable = np.zeros(40 * 64, dtype=np.float32)
+    bad = [t.data_ptr() for t in W]
+    bad[1] = pageable.ctypes.data
+    assert B.bed_eigh_many_f32_pinned(ns, bs, *args(bad), None, cur.cuda_stream,
+                                      [s.cuda_stream for s in side]) == B.BED_ERR_INVALID_ARG
+    two = [x[:2] for x in args([t.data_ptr() for t in W])]
+    assert B.bed_eigh_many_f32_pinned([7, 65], [1, 1], *two, None, cur.cuda_stream,
+                                      [s.cuda_stream for s in side]) == B.BED_ERR_UNSUPPORTED_N
+    torch.cuda.synchronize()
+    assert all(bool((w == -7.0).all()) for w in W)  # nothing ran
+    assert B.bed_eigh_many_f32_pinned(ns, bs, *args([t.data_ptr() for t in W]), None, cur.cuda_stream,
+                                      [s.cuda_stream for s in side]) == B.BED_OK
+    cur.synchronize()
+    for k, (n, b) in enumerate(zip(ns, bs)):
+        if b == 0:
+            continue
+        Wg, Vg, ig = run_gpu(A[k].numpy())
+        assert np.array_equal(W[k].numpy(), Wg) and np.array_equal(V[k].numpy(), Vg)
+        assert np.array_equal(I[k].numpy(), ig)
+    assert B.bed_eigh_many_f32_pinned([], [], [], [], [], None, None, cur.cuda_stream, []) == B.BED_OK
+
+
+def test_many_async_in_flight_matches_synchronous():
+    """Several batched_eigh_many_async calls in flight (more than the stream slots), waited in any
+    order, give the synchronous results bitwise."""
+    calls = [[torch.from_numpy(wl.covariance(30 + 7 * c, n, seed=800 + 10 * c + n)) for n in (64, 20, 33)]
+             for c in range(4)]
+    pend = [B.batched_eigh_many_async(m) for m in calls]
+    dropped = B.batched_eigh_many_async(calls[0])
+    del dropped  # an unfinished call that is dropped waits for its work
+    for c in (2, 0, 3, 1):
+        got = pend[c].wait(return_info=True)
+        ref = B.batched_eigh_many(calls[c], return_info=True)
+        for (W, V, i), (W2, V2, i2) in zip(got, ref):
+            assert torch.equal(W, W2) and torch.equal(V, V2) and torch.equal(i, i2)
+            assert int((i != 0).sum()) == 0
+
+
 @pytest.mark.parametrize("chunks", [0, 2])
 def test_many_batches_host_copy_path(chunks):
     """batched_eigh_many on host tensors through the copy-engine entry point (host_chunks > 0) agrees
