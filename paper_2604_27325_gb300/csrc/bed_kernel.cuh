@@ -61,6 +61,7 @@ struct Smem {
         };
     };
     float sgn[NMAX];
+    float cinv[NMAX];  // merge: 1 / norm of each column of Q^ (P7), applied by P8
     float brho[NB], btol[NB], bsc[NB];  // per merge of a level: |beta|, tolerance, scale
     int rank[NMAX];   // column c of the children -> its sorted position
     int inv[NMAX];    // compacted index -> sorted position
@@ -278,18 +279,37 @@ __device__ __forceinline__ bool ql_leaf(const float* __restrict__ dg, const floa
         z[j] = (j == r) ? 1.f : 0.f;
     }
     bool ok = true;
-    for (int l = 0; l < m; ++l) {
-        for (int iter = 0;; ++iter) {
-            // the first negligible coupling at or after l bounds the unreduced block [l, mm]
-            int mm = m - 1;
+    // One QL step per pass. Eigenvalue l is final once coupling e[l] is negligible; each pass first moves l
+    // past every such coupling, so that the lanes of a warp (up to four leaves) advance together, one
+    // step per pass, rather than waiting for each other at every eigenvalue.
+    int l = 0, iter = 0;
+    for (int pass = 0; pass < 31 * kLeafMax; ++pass) {
+        int mm = m - 1;
+        {
+            bool negl[kLeafMax - 1];
+#pragma unroll
+            for (int j = 0; j < kLeafMax - 1; ++j)
+                negl[j] = (j >= m - 1) || fabsf(e[j]) <= 0x1p-23f * (fabsf(d[j]) + fabsf(d[j + 1]));
+            int ln = m - 1;
 #pragma unroll
             for (int j = kLeafMax - 2; j >= 0; --j)
-                if (j >= l && j < m - 1 && fabsf(e[j]) <= 0x1p-23f * (fabsf(d[j]) + fabsf(d[j + 1]))) mm = j;
-            if (mm == l) break;
-            if (iter >= 30) {
+                if (j >= l && !negl[j]) ln = j;
+            if (ln != l) iter = 0;
+            l = ln;
+            if (l >= m - 1) break;
+            if (iter >= 30) {  // not converged: leave eigenvalue l as it is and go on with the next
                 ok = false;
-                break;
+                ++l;
+                iter = 0;
+                continue;
             }
+            ++iter;
+            // the first negligible coupling after l bounds the unreduced block [l, mm]
+#pragma unroll
+            for (int j = kLeafMax - 2; j >= 0; --j)
+                if (j > l && j < m - 1 && negl[j]) mm = j;
+        }
+        {
             float dl = 0.f, dl1 = 0.f, el = 0.f, dmm = 0.f;
 #pragma unroll
             for (int j = 0; j < kLeafMax; ++j) {
@@ -1134,18 +1154,16 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                         S.M[S.inv[lo + i] * LD + cq] = v;
                         nrm2 = fmaf(v, v, nrm2);
                     }
-                    for (int p = lo + sub; p < hi; p += G)
-                        if (S.defl[p]) S.M[p * LD + cq] = 0.f;
+                    // rows of the deflated poles (compacted indices K ..) are zero
+                    for (int i = K + sub; i < hi - lo; i += G) S.M[S.inv[lo + i] * LD + cq] = 0.f;
                 } else {
                     const int tgt = S.inv[lo + q];
                     for (int p = lo + sub; p < hi; p += G) S.M[p * LD + cq] = (p == tgt) ? 1.f : 0.f;
                 }
             }
+            // the columns are normalized by P8, which scales its products by 1 / |column|
             nrm2 = gsum<G>(nrm2);
-            if (act && q < K) {
-                const float inv = rsqrtf(nrm2);
-                for (int i = sub; i < K; i += G) S.M[S.inv[lo + i] * LD + cq] *= inv;
-            }
+            if (act && sub == 0) S.cinv[cq] = (q < K) ? rsqrtf(nrm2) : 1.f;
             __syncwarp();
             if (act && sub == 0 && S.brot[lb]) {
                 for (int p = hi - 1; p >= lo; --p) {
@@ -1220,7 +1238,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 for (int i = 0; i < PR; ++i)
 #pragma unroll
                     for (int j = 0; j < PC; ++j)
-                        if (r0 + i < rend && q0 + j < qend) S.Q[(r0 + i) * LD + q0 + j] = acc[i][j];
+                        if (r0 + i < rend && q0 + j < qend) S.Q[(r0 + i) * LD + q0 + j] = acc[i][j] * S.cinv[q0 + j];
             }
         }
         team_sync<NT>(bar_id);
