@@ -344,7 +344,7 @@ def run_ours(args, rank, world, local):
     for s in range(K):
         flush.fill_(float(s))  # > L2: every step starts cold
         ev[s][0].record(stream)
-        step(evn[s])
+        step()
         ev[s][1].record(stream)
     torch.cuda.synchronize(dev)
     t_end = time.time()
@@ -353,7 +353,12 @@ def run_ours(args, rank, world, local):
     clocks = ClockSampler.summarize(rows, t_start, t_end)
 
     step_ms = [ev[s][0].elapsed_time(ev[s][-1]) for s in range(K)]
-    # each launch's own duration, on its stream, while the others run beside it
+    # each launch's own duration, on its stream, while the others run beside it: K more steps with an
+    # event pair around every launch, after the timed region (the events slow the step by about 2 %)
+    for s in range(K):
+        flush.fill_(float(s))
+        step(evn[s])
+    torch.cuda.synchronize(dev)
     per_n_ms = {n: [evn[s][n][0].elapsed_time(evn[s][n][1]) for s in range(K)] for n in SIZES}
     total_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = total_ms / K

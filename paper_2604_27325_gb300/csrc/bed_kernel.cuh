@@ -6,19 +6,20 @@
 //   a1  Householder tridiagonalization: A in column-owned register tiles, p = tau A v from the
 //       column sums of each warp's block (A is symmetric), one block barrier per reflector
 //   a2  tear the tridiagonal along the static divide tree (Sec. 2.1, Eq. (2)-(3))
-//   a3  leaves (Sec. 2.2): 1x1; 2x2 by one Jacobi rotation; 3 to 8 rows by implicit QL with Wilkinson shifts
+//   a3  leaves (Sec. 2.2): 1x1; 2x2 by one Jacobi rotation; 3 to 8 rows by implicit QL with
+//       Wilkinson shifts
 //   a4  per merge (Eq. (4)-(5)): coupling vector z, pole ordering, deflation
-//   a5  secular roots (Eq. (8)-(21)): one lane per root, hybrid-section then Halley in coordinates
-//       relative to the nearer pole; a warp stops iterating when all of its lanes have converged
-//       (the GPU form of the progressive batch shrinkage, Eq. (22))
-//   a6  Gu-Eisenstat z-hat (Eq. (25)) and normalized eigenvectors (Eq. (24))
+//   a5  secular roots (Eq. (8)-(21)): one lane per root (G for 16- and 32-row teams), hybrid-section
+//       then Halley in coordinates relative to the nearer pole; a warp stops iterating when all of
+//       its lanes have converged (the GPU form of the progressive batch shrinkage, Eq. (22))
+//   a6  Gu-Eisenstat z-hat (Eq. (25)) and eigenvectors (Eq. (24)), normalized by a7
 //   a7  merge GEMM Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)) in register tiles of 4 rows x 16/G columns
 //   a8  back-transform through the Householder reflectors, 8 at a time as I - Y T Y^T, with each
 //       column of Q held in the registers of its G lanes
 //   a9  ascending order, sign convention, store
 // Thread layouts (NT = NMAX * G threads): "position" pos = tid / G, sub = tid % G: G consecutive
 // lanes share one row / column and combine their partial results with shuffles inside the group;
-// a1 and a7 use their own register tilings and a5 one lane per root, described where they run.
+// a1 and a7 use their own register tilings and a5 its own lanes per root, described where they run.
 #pragma once
 
 #include <atomic>
@@ -1068,10 +1069,11 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             compact();
             team_sync<NT>(bar_id);
         }
-        // P5: secular roots, one lane per root: root t is solved by thread t. Every root repeats the
-        // same scalar step logic around its pole sums, so splitting a root's sums over several lanes
-        // would repeat that logic on each of them; one lane per root issues the fewest instructions.
-        constexpr int GS = 1;  // lanes per root
+        // P5: secular roots, GS lanes per root (root t on threads GS t ..). Every root repeats the same
+        // scalar step logic around its pole sums, so splitting a root's sums over several lanes repeats
+        // that logic on each of them: one lane per root issues the fewest instructions, which pays for
+        // 48 and more rows; smaller teams have too few warps for that and keep G lanes per root.
+        constexpr int GS = (NMAX >= 48) ? 1 : G;  // lanes per root
         if (warp * (32 / GS) < n) {  // warps holding no root skip the phase (the vote inside is per warp)
             const int t = tid / GS;
             const int bt = (t < n) ? plan.blk[L][t] : 0xFF;
