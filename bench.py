@@ -292,13 +292,13 @@ def run_ours(args, rank, world, local):
     side = {n: torch.cuda.Stream(dev) for n in SIZES}
     order = sorted(SIZES, reverse=True)  # the longest launch first
 
-    def launch(n, s=None):
+    def launch(n, s=None, params=None):
         st = B.bed_eigh_f32(Ad[n].data_ptr(), Wd[n].data_ptr(), Vd[n].data_ptr(), Id[n].data_ptr(), BATCH, n,
-                            None, (s or stream).cuda_stream)
+                            params, (s or stream).cuda_stream)
         if st != B.BED_OK:
             raise B.BedError(B.bed_status_string(st) + " " + B.bed_last_cuda_error())
 
-    def step(evs=None):
+    def step(evs=None, params=None):
         fork = torch.cuda.Event()
         fork.record(stream)
         for n in order:
@@ -306,7 +306,7 @@ def run_ours(args, rank, world, local):
             s.wait_event(fork)
             if evs is not None:
                 evs[n][0].record(s)
-            launch(n, s)
+            launch(n, s, params)
             if evs is not None:
                 evs[n][1].record(s)
             join = torch.cuda.Event()
@@ -360,6 +360,26 @@ def run_ours(args, rank, world, local):
         step(evn[s])
     torch.cuda.synchronize(dev)
     per_n_ms = {n: [evn[s][n][0].elapsed_time(evn[s][n][1]) for s in range(K)] for n in SIZES}
+
+    # variant: the merge products on the tensor cores (split-3xTF32), same step, timed the same way
+    tc_params = B.make_params(merge_tensor_cores=1)
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        step(params=tc_params)
+    torch.cuda.synchronize(dev)
+    tc_ms = 0.0
+    for s in range(K):
+        flush.fill_(float(s))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(params=tc_params)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        tc_ms += e0.elapsed_time(e1)
+    tc_ms = max_over_ranks(tc_ms, world)
+    variants = {"merge_tensor_cores_3xtf32": BATCH * len(SIZES) * world * K / (tc_ms / 1e3),
+                "unit": "matrices/s",
+                "what": "uniform workload step with the merge products of Eq. (4) as split-3xTF32 mma.sync"}
     total_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = total_ms / K
     per_step_units = BATCH * len(SIZES)
@@ -501,19 +521,23 @@ def run_ours(args, rank, world, local):
     # its results to page-locked host memory. Pipelined: step s + 1 is submitted before waiting for the
     # results of step s (two calls in flight); the synchronous call is timed as well.
     host = [torch.from_numpy(inputs[n]).pin_memory() for n in SIZES]
+
+    def pipelined(steps):
+        pending = None
+        for _ in range(steps):
+            nxt = B.batched_eigh_many_async(host, slots=3)
+            if pending is not None:
+                pending.wait()
+            pending = nxt
+        pending.wait()
+
     for _ in range(max(1, min(args.warmup, 3))):
         B.batched_eigh_many(host)
-        B.batched_eigh_many_async(host).wait()
+    pipelined(max(args.warmup, 3))
     barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    pending = None
-    for _ in range(K):
-        nxt = B.batched_eigh_many_async(host)
-        if pending is not None:
-            pending.wait()
-        pending = nxt
-    pending.wait()
+    pipelined(K)
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     barrier(world)
@@ -538,6 +562,7 @@ def run_ours(args, rank, world, local):
                    "launch": launch, "parallelism": f"dp{world} (independent matrices)",
                    "l2": "flushed before every step (512 MB write), flush outside the per-step CUDA events"},
         "paths": {"per_size_launches": value, "ragged_persistent_graph": uniform_via_ragged, "unit": "matrices/s"},
+        "variants": variants,
         "ragged": ragged,
         "differentiation": differentiation,
         "serving": serving,

@@ -74,6 +74,13 @@ typedef struct {
                                 have converged (the recast of the paper's progressive batch shrinkage,
                                 Eq. (22)); 0: every warp runs to the iteration caps with converged lanes
                                 idle. Results are bitwise identical either way. */
+    int merge_tensor_cores;  /* 0 (default): the merge products of Eq. (4) on the FP32 FMA pipes; 1: on the
+                                tensor cores as split-3xTF32 (each operand split into two TF32 parts, three
+                                mma.sync m16n8k8 per product, FP32 accumulation). Applies to launches of
+                                bed_eigh_f32* with teams of 4*nmax threads; a merge level with more 16 x 8
+                                tiles than the registers hold, 2*nmax teams, the ragged kernel and the
+                                server use the FP32 products. Results agree with the FP32 path to the
+                                same tolerance, not bitwise. */
 } bed_params;
 
 /* Fills *p with the defaults listed above. */

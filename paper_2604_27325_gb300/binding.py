@@ -40,6 +40,7 @@ class bed_params(C.Structure):
         ("deflation_tol_scale", C.c_float),
         ("threads_per_matrix", C.c_int),
         ("retire_by_vote", C.c_int),
+        ("merge_tensor_cores", C.c_int),
     ]
 
 

@@ -101,8 +101,11 @@ cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int
                         bool bulk, cudaStream_t stream)
 {
 #define BED_CASE(NM, GG)                                                                             \
-    if (nmax == NM && g == GG)                                                                       \
-        return launch_eigh_t<NM, GG>(A, W, V, info, batch, P, kp, counters, bulk, stream);
+    if (nmax == NM && g == GG) {                                                                     \
+        if (GG == 4 && kp.merge_tc)                                                                  \
+            return launch_eigh_t<NM, 4, true>(A, W, V, info, batch, P, kp, counters, bulk, stream);  \
+        return launch_eigh_t<NM, GG>(A, W, V, info, batch, P, kp, counters, bulk, stream);           \
+    }
     BED_CASE(16, 2)
     BED_CASE(16, 4)
     BED_CASE(32, 2)
@@ -130,6 +133,7 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
     if (!(prm->stop_c >= 1.f && prm->stop_c <= 1e6f)) return false;
     if (!(prm->deflation_tol_scale >= 1.f && prm->deflation_tol_scale <= 1e6f)) return false;
     if (prm->retire_by_vote != 0 && prm->retire_by_vote != 1) return false;
+    if (prm->merge_tensor_cores != 0 && prm->merge_tensor_cores != 1) return false;
     kp->k_ms = prm->k_multisection;
     kp->max_sec = prm->max_section_iters;
     kp->max_halley = prm->max_halley_iters;
@@ -137,6 +141,7 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
     kp->stop_c = prm->stop_c;
     kp->defl_c = prm->deflation_tol_scale;
     kp->retire = prm->retire_by_vote;
+    kp->merge_tc = prm->merge_tensor_cores;
     return true;
 }
 
@@ -264,6 +269,7 @@ void bed_default_params(bed_params* p)
     p->deflation_tol_scale = 8.f;
     p->threads_per_matrix = 0;
     p->retire_by_vote = 1;
+    p->merge_tensor_cores = 0;
 }
 
 bed_status bed_eigh_f32(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,

@@ -37,6 +37,7 @@ struct KParams {
     float stop_c;     // Halley stop: |f| <= stop_c * u * err
     float defl_c;     // deflation tolerance scale
     int retire;       // warp-vote retirement of converged roots
+    int merge_tc;     // merge products on the tensor cores (split-3xTF32)
 };
 
 bool build_plan(int n, int leaf_size, Plan* P);
@@ -56,7 +57,8 @@ cudaError_t launch_backward(const float* W, const float* V, const float* gW, con
 // Device address of the allocation-free entry point's scratch on the current device (looked up once).
 cudaError_t noalloc_scratch(void** ptr);
 
-template <int NMAX, int G>
+// TC: the merge products on the tensor cores (split-3xTF32), instantiated for G = 4 teams only.
+template <int NMAX, int G, bool TC = false>
 cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int64_t batch,
                           const Plan& P, const KParams& kp, bed_counters* counters, bool bulk,
                           cudaStream_t stream);

@@ -586,6 +586,49 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
 }
 
 // ---------------------------------------------------------------------------------------------
+// Tensor-core variant of the merge product (a7): split-3xTF32 on mma.sync m16n8k8. Each FP32 operand
+// x is split as x = hi + lo with hi = tf32(x) and lo = tf32(x - hi) (x - hi is exact), and a product
+// is accumulated in FP32 as hi*hi + hi*lo + lo*hi, which keeps about 21 bits of each operand.
+// Fragment layout (PTX ISA, mma.m16n8k8 with .tf32; gid = lane / 4, tig = lane % 4):
+//   A (16 x 8, row):  a0 (gid, tig), a1 (gid + 8, tig), a2 (gid, tig + 4), a3 (gid + 8, tig + 4)
+//   B (8 x 8, col):   b0 (k = tig, n = gid), b1 (k = tig + 4, n = gid)
+//   C (16 x 8, f32):  c0 (gid, 2 tig), c1 (gid, 2 tig + 1), c2 (gid + 8, 2 tig), c3 (gid + 8, 2 tig + 1)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo)
+{
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32_16x8x8(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Tiles of 16 rows x 8 columns of one merge level's products: per merge, the row tiles of the left
+// half, then of the right half, each with all column tiles of the merge.
+__device__ __forceinline__ int tc_level_tiles(const Plan& plan, int L)
+{
+    int t = 0;
+    for (int m = plan.level_start[L]; m < plan.level_start[L + 1]; ++m) {
+        const int lo = plan.m_lo[m], md = plan.m_mid[m], hi = plan.m_hi[m];
+        t += ((md - lo + 15) / 16 + (hi - md + 15) / 16) * ((hi - lo + 7) / 8);
+    }
+    return t;
+}
+
+// ---------------------------------------------------------------------------------------------
 // One matrix, solved by a team of NMAX * G threads (tid = index within the team) that synchronizes
 // on named barrier bar_id. `bar` is the team's mbarrier (initialized by the caller) and `phase` its
 // current phase bit. Returns false only when the staging copy timed out (the caller then stops).
@@ -602,7 +645,148 @@ __device__ __forceinline__ void mbar_init(uint32_t bar)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// a7 on the FP32 FMA pipes. Register tiles: the rows of one half of a merge times its columns form a
+// small product over the half's columns c. The level's tiles (PR rows x PC columns, merges in order, row
+// tiles of the left half, then of the right half, each with all column tiles) are dealt one per thread;
+// per c a thread reads PR entries of Q, one row of Q^ (PC entries) and does PR x PC FMAs. The products
+// are scaled by the reciprocal column norms of Q^ when stored (after the team barrier: Q is read by all).
 template <int NMAX, int G>
+__device__ __forceinline__ void merge_product_fma(Smem<NMAX, G>& S, const Plan& plan, int L, int tid, int bar_id)
+{
+    constexpr int NT = NMAX * G;
+    constexpr int LD = Smem<NMAX, G>::LD;
+    constexpr int PR = 4;
+    constexpr int PC = 16 / G;
+    int r0 = 0, rend = 0, c0 = 0, c1 = 0, q0 = 0, qend = 0;
+    bool have = false;
+    {
+        int tbase = 0;
+        for (int m = plan.level_start[L]; m < plan.level_start[L + 1]; ++m) {
+            const int lo = plan.m_lo[m], md = plan.m_mid[m], hi = plan.m_hi[m];
+            const int rtl = (md - lo + PR - 1) / PR, rtr = (hi - md + PR - 1) / PR;
+            const int ctn = (hi - lo + PC - 1) / PC;
+            const int cnt = (rtl + rtr) * ctn;
+            if (tid >= tbase && tid < tbase + cnt) {
+                const int u = tid - tbase;
+                const int rr = u / ctn, ct = u - rr * ctn;
+                const bool left = rr < rtl;
+                r0 = left ? lo + PR * rr : md + PR * (rr - rtl);
+                rend = left ? md : hi;
+                c0 = left ? lo : md;
+                c1 = left ? md : hi;
+                q0 = lo + PC * ct;
+                qend = hi;
+                have = true;
+            }
+            tbase += cnt;
+        }
+    }
+    float acc[PR][PC];
+#pragma unroll
+    for (int i = 0; i < PR; ++i)
+#pragma unroll
+        for (int j = 0; j < PC; ++j) acc[i][j] = 0.f;
+    if (have) {
+        // rows past rend and columns past qend read padding or neighbouring entries; their
+        // sums are never stored
+        const float* qrow = S.Q + r0 * LD;
+        for (int c = c0; c < c1; ++c) {
+            const float* mrow = S.M + S.rank[c] * LD + q0;
+            float mv[PC];
+#pragma unroll
+            for (int j = 0; j < PC; ++j) mv[j] = mrow[j];
+#pragma unroll
+            for (int i = 0; i < PR; ++i) {
+                const float qv = qrow[i * LD + c];
+#pragma unroll
+                for (int j = 0; j < PC; ++j) acc[i][j] = fmaf(qv, mv[j], acc[i][j]);
+            }
+        }
+    }
+    team_sync<NT>(bar_id);
+    if (have) {
+#pragma unroll
+        for (int i = 0; i < PR; ++i)
+#pragma unroll
+            for (int j = 0; j < PC; ++j)
+                if (r0 + i < rend && q0 + j < qend) S.Q[(r0 + i) * LD + q0 + j] = acc[i][j] * S.cinv[q0 + j];
+    }
+}
+
+// a7 on the tensor cores (split-3xTF32, see above): tiles of 16 rows x 8 columns in the order of
+// tc_level_tiles; warp w computes tiles w, w + NW, ... (at most TPW) in registers, then, after the team
+// barrier, stores them scaled by the reciprocal column norms of Q^.
+template <int NMAX, int G, int TPW>
+__device__ __forceinline__ void merge_product_tc(Smem<NMAX, G>& S, const Plan& plan, int L, int tid, int bar_id)
+{
+    constexpr int NT = NMAX * G;
+    constexpr int NW = NT / 32;
+    constexpr int LD = Smem<NMAX, G>::LD;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    // tile t of this level: rows [r0, rend), columns from q0 (below qend), inner index over [c0, c1)
+    auto tile = [&](int t, int& r0, int& rend, int& c0, int& c1, int& q0, int& qend) {
+        r0 = rend = c0 = c1 = q0 = qend = 0;
+        int tbase = 0;
+        for (int m = plan.level_start[L]; m < plan.level_start[L + 1]; ++m) {
+            const int lo = plan.m_lo[m], md = plan.m_mid[m], hi = plan.m_hi[m];
+            const int rtl = (md - lo + 15) / 16, rtr = (hi - md + 15) / 16, ctn = (hi - lo + 7) / 8;
+            const int cnt = (rtl + rtr) * ctn;
+            if (t >= tbase && t < tbase + cnt) {
+                const int u = t - tbase;
+                const int rr = u / ctn, ct = u - rr * ctn;
+                const bool left = rr < rtl;
+                r0 = left ? lo + 16 * rr : md + 16 * (rr - rtl);
+                rend = left ? md : hi;
+                c0 = left ? lo : md;
+                c1 = left ? md : hi;
+                q0 = lo + 8 * ct;
+                qend = hi;
+            }
+            tbase += cnt;
+        }
+    };
+    float acc[TPW][4];
+#pragma unroll
+    for (int j = 0; j < TPW; ++j) {
+        acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+        int r0, rend, c0, c1, q0, qend;
+        tile(warp + j * NW, r0, rend, c0, c1, q0, qend);  // past the last tile: c0 == c1, nothing to do
+        const int ra = r0 + gid, rb = ra + 8, nq = q0 + gid;
+        for (int kc = c0; kc < c1; kc += 8) {
+            const int ka = kc + tig, kb = ka + 4;
+            const float x0 = (ra < rend && ka < c1) ? S.Q[ra * LD + ka] : 0.f;
+            const float x1 = (rb < rend && ka < c1) ? S.Q[rb * LD + ka] : 0.f;
+            const float x2 = (ra < rend && kb < c1) ? S.Q[ra * LD + kb] : 0.f;
+            const float x3 = (rb < rend && kb < c1) ? S.Q[rb * LD + kb] : 0.f;
+            const float y0 = (ka < c1 && nq < qend) ? S.M[S.rank[ka] * LD + nq] : 0.f;
+            const float y1 = (kb < c1 && nq < qend) ? S.M[S.rank[kb] * LD + nq] : 0.f;
+            uint32_t ah[4], al[4], bh[2], bl[2];
+            split_tf32(x0, ah[0], al[0]);
+            split_tf32(x1, ah[1], al[1]);
+            split_tf32(x2, ah[2], al[2]);
+            split_tf32(x3, ah[3], al[3]);
+            split_tf32(y0, bh[0], bl[0]);
+            split_tf32(y1, bh[1], bl[1]);
+            mma_tf32_16x8x8(acc[j], al, bh);
+            mma_tf32_16x8x8(acc[j], ah, bl);
+            mma_tf32_16x8x8(acc[j], ah, bh);
+        }
+    }
+    team_sync<NT>(bar_id);
+#pragma unroll
+    for (int j = 0; j < TPW; ++j) {
+        int r0, rend, c0, c1, q0, qend;
+        tile(warp + j * NW, r0, rend, c0, c1, q0, qend);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int r = r0 + gid + ((e & 2) ? 8 : 0), q = q0 + 2 * tig + (e & 1);
+            if (r < rend && q < qend) S.Q[r * LD + q] = acc[j][e] * S.cinv[q];
+        }
+    }
+}
+
+template <int NMAX, int G, bool TC = false>
 __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan, const KParams& kp, const int tid,
                                              const int bar_id, const uint32_t bar, uint32_t& phase,
                                              const float* __restrict__ Ab, float* __restrict__ Wb,
@@ -1180,68 +1364,15 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             }
         }
         team_sync<NT>(bar_id);
-        // P8: Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)); rows of Q^ are gathered through the pole order.
-        // Register tiles: the rows of one half of a merge times its columns form a small product over
-        // the half's columns c. The level's tiles (PR rows x PC columns, merges in order, row tiles of
-        // the left half, then of the right half, each with all column tiles) are dealt one per thread;
-        // per c a thread reads PR entries of Q, one row of Q^ (PC entries) and does PR x PC FMAs.
-        {
-            constexpr int PR = 4;
-            constexpr int PC = 16 / G;
-            int r0 = 0, rend = 0, c0 = 0, c1 = 0, q0 = 0, qend = 0;
-            bool have = false;
-            {
-                int tbase = 0;
-                for (int m = plan.level_start[L]; m < plan.level_start[L + 1]; ++m) {
-                    const int lo = plan.m_lo[m], md = plan.m_mid[m], hi = plan.m_hi[m];
-                    const int rtl = (md - lo + PR - 1) / PR, rtr = (hi - md + PR - 1) / PR;
-                    const int ctn = (hi - lo + PC - 1) / PC;
-                    const int cnt = (rtl + rtr) * ctn;
-                    if (tid >= tbase && tid < tbase + cnt) {
-                        const int u = tid - tbase;
-                        const int rr = u / ctn, ct = u - rr * ctn;
-                        const bool left = rr < rtl;
-                        r0 = left ? lo + PR * rr : md + PR * (rr - rtl);
-                        rend = left ? md : hi;
-                        c0 = left ? lo : md;
-                        c1 = left ? md : hi;
-                        q0 = lo + PC * ct;
-                        qend = hi;
-                        have = true;
-                    }
-                    tbase += cnt;
-                }
-            }
-            float acc[PR][PC];
-#pragma unroll
-            for (int i = 0; i < PR; ++i)
-#pragma unroll
-                for (int j = 0; j < PC; ++j) acc[i][j] = 0.f;
-            if (have) {
-                // rows past rend and columns past qend read padding or neighbouring entries; their
-                // sums are never stored
-                const float* qrow = S.Q + r0 * LD;
-                for (int c = c0; c < c1; ++c) {
-                    const float* mrow = S.M + S.rank[c] * LD + q0;
-                    float mv[PC];
-#pragma unroll
-                    for (int j = 0; j < PC; ++j) mv[j] = mrow[j];
-#pragma unroll
-                    for (int i = 0; i < PR; ++i) {
-                        const float qv = qrow[i * LD + c];
-#pragma unroll
-                        for (int j = 0; j < PC; ++j) acc[i][j] = fmaf(qv, mv[j], acc[i][j]);
-                    }
-                }
-            }
-            team_sync<NT>(bar_id);
-            if (have) {
-#pragma unroll
-                for (int i = 0; i < PR; ++i)
-#pragma unroll
-                    for (int j = 0; j < PC; ++j)
-                        if (r0 + i < rend && q0 + j < qend) S.Q[(r0 + i) * LD + q0 + j] = acc[i][j] * S.cinv[q0 + j];
-            }
+        // P8: Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)); rows of Q^ are gathered through the pole order
+        if constexpr (TC) {
+            constexpr int TPW = (32 / NW < 2) ? 2 : ((32 / NW > 8) ? 8 : 32 / NW);  // tiles per warp
+            if (tc_level_tiles(plan, L) <= TPW * NW)
+                merge_product_tc<NMAX, G, TPW>(S, plan, L, tid, bar_id);
+            else
+                merge_product_fma<NMAX, G>(S, plan, L, tid, bar_id);
+        } else {
+            merge_product_fma<NMAX, G>(S, plan, L, tid, bar_id);
         }
         team_sync<NT>(bar_id);
     }
@@ -1468,7 +1599,7 @@ constexpr int eigh_min_blocks()
     return m < 1 ? 1 : m;
 }
 
-template <int NMAX, int G>
+template <int NMAX, int G, bool TC>
 __global__ void __launch_bounds__(NMAX * G, eigh_min_blocks<NMAX, G>())
     eigh_kernel(const float* __restrict__ A, float* __restrict__ W, float* __restrict__ V,
                 int32_t* __restrict__ info, int64_t batch, const __grid_constant__ Plan plan,
@@ -1484,20 +1615,20 @@ __global__ void __launch_bounds__(NMAX * G, eigh_min_blocks<NMAX, G>())
         __syncthreads();
     }
     for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
-        if (!solve_matrix<NMAX, G>(S, plan, kp, threadIdx.x, 0, bar, phase, A + b * (int64_t)n * n,
+        if (!solve_matrix<NMAX, G, TC>(S, plan, kp, threadIdx.x, 0, bar, phase, A + b * (int64_t)n * n,
                                    W + b * (int64_t)n, V + b * (int64_t)n * n, info ? info + b : nullptr,
                                    counters, bulk != 0))
             return;
     }
 }
 
-template <int NMAX, int G>
+template <int NMAX, int G, bool TC>
 cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int64_t batch,
                           const Plan& P, const KParams& kp, bed_counters* counters, bool bulk,
                           cudaStream_t stream)
 {
     const size_t smem = sizeof(Smem<NMAX, G>);
-    auto kern = eigh_kernel<NMAX, G>;
+    auto kern = eigh_kernel<NMAX, G, TC>;
     // the function attributes are per device: set them on the first launch there (setting them again
     // from a racing thread is harmless), keeping later launches to the launch itself
     static std::atomic<unsigned long long> configured{0};

@@ -381,6 +381,38 @@ def test_many_batches_host_copy_path(chunks):
         assert torch.equal(W, W2) and torch.equal(V, V2) and torch.equal(i, i2)
 
 
+# ------------------------------------------------- merge products on the tensor cores (split-3xTF32)
+
+
+@pytest.mark.parametrize("leaf", [1, 2, 8])
+def test_tensor_core_merges_every_n(leaf):
+    """merge_tensor_cores = 1: every n (all four team sizes; with leaf 1 the deepest level of a large
+    matrix has more tiles than the registers hold and takes the FP32 products) within the tolerance."""
+    p = B.make_params(leaf_size=leaf, merge_tensor_cores=1)
+    for n in range(1, 65):
+        A = np.concatenate([wl.covariance(3, n, seed=9400 + n), wl.known_spectrum(2, n, seed=9500 + n)[0]])
+        W, V, info = run_gpu(A, p)
+        Wo, Vo = run_oracle(A)
+        assert_parity(A, W, V, info, Wo, Vo, f"tensor-core merges leaf={leaf} n={n}")
+
+
+@pytest.mark.parametrize("n", [16, 32, 48, 64])
+def test_tensor_core_merges_uniform_workload(n):
+    A = wl.covariance(512, n)
+    W, V, info = run_gpu(A, B.make_params(merge_tensor_cores=1))
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W, V, info, Wo, Vo, f"tensor-core merges covariance 512 x {n}")
+
+
+@pytest.mark.parametrize("name", ["zero", "identity", "diagonal", "repeated", "rank_one", "block_diagonal", "toeplitz"])
+def test_tensor_core_merges_degenerate_inputs(name):
+    for n in (3, 9, 17, 37, 64):
+        A = wl.special_cases(n)[name][None].repeat(2, axis=0)
+        W, V, info = run_gpu(A, B.make_params(merge_tensor_cores=1))
+        Wo, Vo = run_oracle(A)
+        assert_parity(A, W, V, info, Wo, Vo, f"tensor-core merges {name} n={n}")
+
+
 @pytest.mark.parametrize("n", [5, 16, 40, 64])
 def test_power_of_two_scaling_is_exact(n):
     """The kernel scales every matrix by a power of two before solving and back after: A 2^e gives
