@@ -9,7 +9,7 @@
 //   a3  leaves (Sec. 2.2): 1x1; 2x2 by one Jacobi rotation; 3 to 8 rows by implicit QL with
 //       Wilkinson shifts
 //   a4  per merge (Eq. (4)-(5)): coupling vector z, pole ordering, deflation
-//   a5  secular roots (Eq. (8)-(21)): one lane per root (G for 16- and 32-row teams), hybrid-section
+//   a5  secular roots (Eq. (8)-(21)): 1 or 2 lanes per root (G for 16- and 32-row teams), hybrid-section
 //       then Halley in coordinates relative to the nearer pole; a warp stops iterating when all of
 //       its lanes have converged (the GPU form of the progressive batch shrinkage, Eq. (22))
 //   a6  Gu-Eisenstat z-hat (Eq. (25)) and eigenvectors (Eq. (24)), normalized by a7
@@ -1255,9 +1255,10 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         }
         // P5: secular roots, GS lanes per root (root t on threads GS t ..). Every root repeats the same
         // scalar step logic around its pole sums, so splitting a root's sums over several lanes repeats
-        // that logic on each of them: one lane per root issues the fewest instructions, which pays for
-        // 48 and more rows; smaller teams have too few warps for that and keep G lanes per root.
-        constexpr int GS = (NMAX >= 48) ? 1 : G;  // lanes per root
+        // that logic on each of them: fewer lanes per root issue fewer instructions. Measured best:
+        // two lanes per root for 64-row teams (the roots then fill four warps, one per scheduler of
+        // the SM), one for 48 rows; 16- and 32-row teams have too few warps and keep G lanes per root.
+        constexpr int GS = (NMAX == 64) ? 2 : ((NMAX == 48) ? 1 : G);  // lanes per root
         if (warp * (32 / GS) < n) {  // warps holding no root skip the phase (the vote inside is per warp)
             const int t = tid / GS;
             const int bt = (t < n) ? plan.blk[L][t] : 0xFF;
