@@ -166,7 +166,8 @@ bed_status bed_eigh_f32_pinned(const float* A_host, float* W_host, float* V_host
  *   side, nside      streams the launches run on, largest n first, batch j of that order on
  *                    side[j % nside], so that batches of different n run side by side
  * Every argument of every batch is checked before anything is enqueued (BED_ERR_UNSUPPORTED_N,
- * BED_ERR_INVALID_ARG); a CUDA error (BED_ERR_CUDA) may leave earlier launches of the call enqueued.
+ * BED_ERR_INVALID_ARG); after a CUDA error (BED_ERR_CUDA) earlier launches of the call may stay
+ * enqueued, still joined to `origin`.
  * The results are in host memory once `origin` has reached this call's work.
  */
 bed_status bed_eigh_many_f32_pinned(int count, const int* ns, const int64_t* batches, const float* const* A_host,

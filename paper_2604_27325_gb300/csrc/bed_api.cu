@@ -449,18 +449,19 @@ bed_status bed_eigh_many_f32_pinned(int count, const int* ns, const int64_t* bat
         e = cudaStreamWaitEvent(side[s], ev->fork, 0);
         if (e != cudaSuccess) return bed::cuda_fail(e);
     }
-    for (size_t j = 0; j < order.size(); ++j) {
+    bed_status st = BED_OK;
+    for (size_t j = 0; j < order.size() && st == BED_OK; ++j) {
         const int k = order[j];
-        const bed_status st = bed::eigh_common(dp[k].A, dp[k].W, dp[k].V, dp[k].info, batches[k], ns[k], p, nullptr,
-                                               side[j % used], true);
-        if (st != BED_OK) return st;
+        st = bed::eigh_common(dp[k].A, dp[k].W, dp[k].V, dp[k].info, batches[k], ns[k], p, nullptr, side[j % used],
+                              true);
     }
+    // join even after a failed launch, so that `origin` still orders after whatever was enqueued
     for (int s = 0; s < used; ++s) {
         e = cudaEventRecord(ev->join, side[s]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, ev->join, 0);
-        if (e != cudaSuccess) return bed::cuda_fail(e);
+        if (e != cudaSuccess && st == BED_OK) st = bed::cuda_fail(e);
     }
-    return BED_OK;
+    return st;
 }
 
 bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count,
