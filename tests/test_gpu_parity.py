@@ -370,6 +370,27 @@ def test_many_async_in_flight_matches_synchronous():
             assert int((i != 0).sum()) == 0
 
 
+def test_uniform_workload_end_to_end_path_at_full_size():
+    """The benchmark's end-to-end configuration: the uniform workload (512 matrices at each of
+    n = 16, 32, 48, 64) from page-locked host memory through batched_eigh_many_async with two calls in
+    flight; every result equals the device path bitwise, and a sample of each size matches the oracle."""
+    sizes = (16, 32, 48, 64)
+    host = [torch.from_numpy(wl.covariance(512, n)).pin_memory() for n in sizes]
+    p1 = B.batched_eigh_many_async(host)
+    p2 = B.batched_eigh_many_async(host)
+    r1 = p1.wait(return_info=True)
+    r2 = p2.wait(return_info=True)
+    rng = np.random.default_rng(5)
+    for n, A, (W, V, info), (W2, V2, info2) in zip(sizes, host, r1, r2):
+        Wd, Vd, infod = run_gpu(A.numpy())
+        assert np.array_equal(W.numpy(), Wd) and np.array_equal(V.numpy(), Vd) and np.array_equal(info.numpy(), infod)
+        assert torch.equal(W, W2) and torch.equal(V, V2)
+        idx = np.sort(rng.choice(512, 24, replace=False))
+        An = A.numpy()[idx]
+        Wo, Vo = run_oracle(An)
+        assert_parity(An, W.numpy()[idx], V.numpy()[idx], info.numpy()[idx], Wo, Vo, f"end-to-end path n={n}")
+
+
 @pytest.mark.parametrize("chunks", [0, 2])
 def test_many_batches_host_copy_path(chunks):
     """batched_eigh_many on host tensors through the copy-engine entry point (host_chunks > 0) agrees
