@@ -338,11 +338,16 @@ def run_ours(args, rank, world, local):
     # the step (fork, one launch per n on its own stream, join) captured once as a CUDA graph and replayed
     # on the timing stream: the same four kernels, without the per-step host enqueue between them
     cap = torch.cuda.Stream(dev)
-    cap.wait_stream(stream)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=cap):
-        step(origin=cap)
-    torch.cuda.synchronize(dev)
+
+    def capture_step(evs=None, params=None):
+        g = torch.cuda.CUDAGraph()
+        cap.wait_stream(stream)
+        with torch.cuda.graph(g, stream=cap):
+            step(evs, params=params, origin=cap)
+        torch.cuda.synchronize(dev)
+        return g
+
+    graph = capture_step()
     for i in range(args.warmup):
         flush.fill_(float(i))
         graph.replay()
@@ -369,31 +374,43 @@ def run_ours(args, rank, world, local):
     clocks = ClockSampler.summarize(rows, t_start, t_end)
 
     step_ms = [ev[s][0].elapsed_time(ev[s][-1]) for s in range(K)]
-    # each launch's own duration, on its stream, while the others run beside it: K more steps with an
-    # event pair around every launch, after the timed region (the events slow the step by about 2 %); each
-    # step is enqueued on an idle GPU, as a graph replay starts its four launches without host gaps
-    for s in range(K):
-        flush.fill_(float(s))
-        step(evn[s])
+    # each launch's own duration, on its stream, while the others run beside it: after the timed region,
+    # K more steps replayed back to back, each from its own capture of the same step with a timing event
+    # pair (recorded as graph nodes) around every launch
+    try:
+        KE = min(K, 100)
+        evg = [{n: (torch.cuda.Event(enable_timing=True, external=True),
+                    torch.cuda.Event(enable_timing=True, external=True)) for n in SIZES} for _ in range(KE)]
+        graphs_t = [capture_step(evg[s]) for s in range(KE)]
+        for s in range(KE):
+            flush.fill_(float(s))
+            graphs_t[s].replay()
         torch.cuda.synchronize(dev)
-    per_n_ms = {n: [evn[s][n][0].elapsed_time(evn[s][n][1]) for s in range(K)] for n in SIZES}
+        per_n_ms = {n: [evg[s][n][0].elapsed_time(evg[s][n][1]) for s in range(KE)] for n in SIZES}
+        per_n_how = "graph replays with timing-event nodes around each launch"
+        del graphs_t
+    except (TypeError, RuntimeError):  # no external events in this PyTorch: eager steps on an idle GPU
+        for s in range(K):
+            flush.fill_(float(s))
+            step(evn[s])
+            torch.cuda.synchronize(dev)
+        per_n_ms = {n: [evn[s][n][0].elapsed_time(evn[s][n][1]) for s in range(K)] for n in SIZES}
+        per_n_how = "eager steps, each on an idle GPU, with an event pair around each launch"
 
     # variant: the merge products on the tensor cores (split-3xTF32), same step, timed the same way
-    tc_params = B.make_params(merge_tensor_cores=1)
+    tc_graph = capture_step(params=B.make_params(merge_tensor_cores=1))
     for i in range(args.warmup):
         flush.fill_(float(i))
-        step(params=tc_params)
+        tc_graph.replay()
     torch.cuda.synchronize(dev)
-    tc_ms = 0.0
+    tc_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
     for s in range(K):
         flush.fill_(float(s))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(params=tc_params)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        tc_ms += e0.elapsed_time(e1)
-    tc_ms = max_over_ranks(tc_ms, world)
+        tc_ev[s][0].record(stream)
+        tc_graph.replay()
+        tc_ev[s][1].record(stream)
+    torch.cuda.synchronize(dev)
+    tc_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in tc_ev), world)
     variants = {"merge_tensor_cores_3xtf32": BATCH * len(SIZES) * world * K / (tc_ms / 1e3),
                 "unit": "matrices/s",
                 "what": "uniform workload step with the merge products of Eq. (4) as split-3xTF32 mma.sync"}
@@ -585,6 +602,7 @@ def run_ours(args, rank, world, local):
         "differentiation": differentiation,
         "serving": serving,
         "per_n_ms": {str(n): statistics.mean(v) for n, v in per_n_ms.items()},
+        "per_n_ms_from": per_n_how,
         "kbar": {str(n): kbar[n] for n in SIZES},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic,
