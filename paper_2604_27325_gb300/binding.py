@@ -340,10 +340,13 @@ def batched_eigh(A: torch.Tensor, params: bed_params | None = None, check: bool 
 
     Returns ``(W, V)`` with W ascending and the eigenvectors in the columns of V (torch.linalg.eigh
     conventions); with ``return_info`` also the int32 per-matrix status flags. A CUDA tensor is solved
-    in place on the current stream; a CPU tensor is copied to the current CUDA device through pinned
-    memory, solved, and the results are copied back (the end-to-end path). ``check=True`` synchronizes
-    and raises if any matrix reports a non-zero info.
+    in place on the current stream; a CPU tensor is solved from page-locked host memory by the
+    zero-copy entry point (the kernel reads it and writes the results to host memory; with
+    ``counters``, which live on the device, it is copied to the device and back instead).
+    ``check=True`` synchronizes and raises if any matrix reports a non-zero info.
     """
+    if not A.is_cuda and counters is None and A.dtype == torch.float32:
+        return batched_eigh_many([A], params, check, return_info)[0]
     out = _eigh_enqueue(A, params, counters)
     if out[3]:
         torch.cuda.current_stream(out[0].device if out[0].is_cuda else None).synchronize()
