@@ -180,7 +180,8 @@ bed_status bed_eigh_many_f32_pinned(int count, const int* ns, const int64_t* bat
  *
  * Work is handed out in units of one thread block (256 threads) split into teams, one matrix per team:
  *   team type 0: 1 team of 256 threads, any n <= 64;   type 1: 2 teams of 128 threads, n <= 32;
- *   type 2: 4 teams of 64 threads, n <= 16;            type 3: 8 teams of 32 threads, n <= 16.
+ *   type 2: 4 teams of 64 threads, n <= 16;            type 3: 8 teams of 32 threads, n <= 16;
+ *   type 4: 1 team of 192 threads (the block's other 64 threads idle), n <= 48.
  * bed_ragged_tuning chooses the team type and the leaf size of the divide tree for every n (entries
  * 1..64 are used; an autotuner fills it by measurement).
  */
@@ -189,7 +190,8 @@ typedef struct {
     unsigned char leaf[65]; /* leaf size (1..8) for each n */
 } bed_ragged_tuning;
 
-/* Fills *t with the built-in choice: type 2 for n <= 16, type 1 for n <= 32, type 0 above; leaf 8. */
+/* Fills *t with the built-in choice: type 2 for n <= 16, type 1 for n <= 32, type 4 for n <= 48, type 0
+ * above; leaf 8. */
 void bed_ragged_default_tuning(bed_ragged_tuning* t);
 
 /* Bytes of device workspace bed_eigh_ragged_f32 needs for `count` matrices (a multiple of 256). */

@@ -1,7 +1,7 @@
 """Autotuner for ragged launches: picks, for every n, the team shape and leaf size by measurement.
 
 For each n the candidates are the team types whose size class holds n (one 256-thread team, two
-128-thread, four 64-thread or eight 32-thread teams per block) times three leaf sizes of the divide
+128-thread, four 64-thread or eight 32-thread teams per block, or one 192-thread team) times three leaf sizes of the divide
 tree (Sec. 2.1-2.2: 2x2 leaves, or QL leaves of up to 4 or 8 rows). Each candidate solves a uniform batch of seeded covariance
 matrices of that n through the ragged entry point; the fastest per-matrix time wins. Results are kept
 as JSON keyed by the GPU's name, and :func:`load` turns them into a ``bed_ragged_tuning``.
@@ -17,7 +17,7 @@ import torch
 from . import binding as B
 from . import workloads
 
-TEAM_CAP = {0: 64, 1: 32, 2: 16, 3: 16}
+TEAM_CAP = {0: 64, 1: 32, 2: 16, 3: 16, 4: 48}
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_DIR = os.path.join(HERE, "tuning")
 

@@ -202,8 +202,8 @@ bool tuning_valid(const bed_ragged_tuning& t)
     for (int n = 1; n <= kMaxN; ++n) {
         if (t.leaf[n] < 1 || t.leaf[n] > kMaxLeaf) return false;
         const int tt = t.team[n];
-        if (tt > 3) return false;
-        const int cap = tt == 0 ? 64 : (tt == 1 ? 32 : 16);
+        if (tt > 4) return false;
+        const int cap = tt == 0 ? 64 : (tt == 4 ? 48 : (tt == 1 ? 32 : 16));
         if (n > cap) return false;
     }
     return true;
@@ -220,7 +220,7 @@ void bed_ragged_default_tuning(bed_ragged_tuning* t)
     if (!t) return;
     std::memset(t, 0, sizeof *t);
     for (int n = 0; n <= bed::kMaxN; ++n) {
-        t->team[n] = static_cast<unsigned char>(n <= 16 ? 2 : (n <= 32 ? 1 : 0));
+        t->team[n] = static_cast<unsigned char>(n <= 16 ? 2 : (n <= 32 ? 1 : (n <= 48 ? 4 : 0)));
         t->leaf[n] = 8;
     }
 }

@@ -6,6 +6,7 @@
 //   team type 1: two teams of 128 threads (NMAX 32, 4 lanes per row)
 //   team type 2: four teams of 64 threads (NMAX 16, 4 lanes per row)
 //   team type 3: eight teams of 32 threads (NMAX 16, 2 lanes per row)
+//   team type 4: one team of 192 threads (NMAX 48, 4 lanes per row; the block's last 64 threads idle)
 // Each team runs the same per-matrix code as the uniform launch (solve_matrix) on its own slice of
 // shared memory, with its own named barrier and mbarrier. A one-block pre-kernel sorts the matrices by
 // (team type, n descending) into the workspace so that the costliest units are handed out first, and
@@ -18,11 +19,10 @@
 namespace bed {
 
 constexpr int kRaggedThreads = 256;
-constexpr int kTeamTypes = 4;
+constexpr int kTeamTypes = 5;
 constexpr int kMaxTeams = 8;
 
-__host__ __device__ constexpr int team_count(int t) { return t == 0 ? 1 : (t == 1 ? 2 : (t == 2 ? 4 : 8)); }
-__host__ __device__ constexpr int team_nmax(int t) { return t == 0 ? 64 : (t == 1 ? 32 : 16); }
+__host__ __device__ constexpr int team_count(int t) { return (t == 0 || t == 4) ? 1 : (t == 1 ? 2 : (t == 2 ? 4 : 8)); }
 
 template <int NMAX, int G>
 __host__ __device__ constexpr size_t slice_bytes()
@@ -31,8 +31,9 @@ __host__ __device__ constexpr size_t slice_bytes()
 }
 
 __host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t kRaggedSmem = cmax(cmax(slice_bytes<64, 4>(), 2 * slice_bytes<32, 4>()),
-                                    cmax(4 * slice_bytes<16, 4>(), 8 * slice_bytes<16, 2>()));
+constexpr size_t kRaggedSmem = cmax(cmax(cmax(slice_bytes<64, 4>(), 2 * slice_bytes<32, 4>()),
+                                         cmax(4 * slice_bytes<16, 4>(), 8 * slice_bytes<16, 2>())),
+                                    slice_bytes<48, 4>());
 
 // Divide trees for every n and every leaf size, written once per device (setup before first use).
 __device__ Plan g_plans[kMaxLeaf][kMaxN + 1];
@@ -42,7 +43,7 @@ struct RaggedHeader {
     unsigned int total_units;
     unsigned int unit_start[kTeamTypes + 1];  // first unit of each team type
     unsigned int mat_start[kTeamTypes + 1];   // first position in `order` of each team type
-    unsigned int pad[4];
+    unsigned int pad[2];
 };
 static_assert(sizeof(RaggedHeader) == 64, "workspace header is 64 bytes");
 
@@ -162,7 +163,10 @@ __global__ void __launch_bounds__(kRaggedThreads, 4)
         case 0: ok = run_team<64, 4>(smem_raw, a, tune, kp, 0, tid, first, last, mbars, phases); break;
         case 1: ok = run_team<32, 4>(smem_raw, a, tune, kp, tid / 128, tid % 128, first, last, mbars, phases); break;
         case 2: ok = run_team<16, 4>(smem_raw, a, tune, kp, tid / 64, tid % 64, first, last, mbars, phases); break;
-        default: ok = run_team<16, 2>(smem_raw, a, tune, kp, tid / 32, tid % 32, first, last, mbars, phases); break;
+        case 3: ok = run_team<16, 2>(smem_raw, a, tune, kp, tid / 32, tid % 32, first, last, mbars, phases); break;
+        default:  // one 192-thread team; the last 64 threads wait at the block barrier below
+            if (tid < 192) ok = run_team<48, 4>(smem_raw, a, tune, kp, 0, tid, first, last, mbars, phases);
+            break;
         }
         if (!ok) s_stop = 1;  // a staging copy timed out: this block stops taking work
         // the next unit may stage a matrix by bulk copy into memory any thread wrote in this one

@@ -184,8 +184,10 @@ void launch(bed_server* s, int si, std::vector<Request*>& batch)
             bed_params p = s->params;
             if (s->cfg.mode == 0) {
                 // the team shape and leaf size the ragged kernel gives this n, so that a request's results
-                // do not depend on whether it was batched with others (team t has 256 >> t threads)
-                p.threads_per_matrix = 256 >> s->tuning.team[r->n];
+                // do not depend on whether it was batched with others (team types 0..4 have 256, 128, 64,
+                // 32 and 192 threads)
+                const int tt = s->tuning.team[r->n];
+                p.threads_per_matrix = (tt == 4) ? 192 : (256 >> tt);
                 p.leaf_size = s->tuning.leaf[r->n];
             }
             st = bed_eigh_f32(A + r->a_off, W + r->w_off, V + r->a_off, sl.info_d, r->b, r->n, &p, sl.stream);

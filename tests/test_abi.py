@@ -132,8 +132,14 @@ def test_ragged_validation_before_launch():
     assert B.bed_eigh_ragged_f32(**{**args, "ns_ptr": 0}) == B.BED_ERR_INVALID_ARG
     assert B.bed_eigh_ragged_f32(**{**args, "V_ptr": FAKE}) == B.BED_ERR_INVALID_ARG
     t = B.bed_ragged_default_tuning()
-    assert [t.team[n] for n in (1, 16, 17, 32, 33, 64)] == [2, 2, 1, 1, 0, 0]
+    assert [t.team[n] for n in (1, 16, 17, 32, 33, 48, 49, 64)] == [2, 2, 1, 1, 4, 4, 0, 0]
     t.team[20] = 2  # a 64-thread team (n <= 16) cannot hold n = 20
+    assert B.bed_eigh_ragged_f32(**{**args, "tuning": t}) == B.BED_ERR_INVALID_ARG
+    t = B.bed_ragged_default_tuning()
+    t.team[49] = 4  # the 192-thread team holds n <= 48
+    assert B.bed_eigh_ragged_f32(**{**args, "tuning": t}) == B.BED_ERR_INVALID_ARG
+    t = B.bed_ragged_default_tuning()
+    t.team[7] = 5  # no such team type
     assert B.bed_eigh_ragged_f32(**{**args, "tuning": t}) == B.BED_ERR_INVALID_ARG
     t = B.bed_ragged_default_tuning()
     t.leaf[5] = 9

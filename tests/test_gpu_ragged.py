@@ -13,7 +13,7 @@ from parity import assert_parity
 pytestmark = pytest.mark.gpu
 
 NTHREADS = os.cpu_count() or 1
-TEAM_THREADS = {0: 256, 1: 128, 2: 64, 3: 32}
+TEAM_THREADS = {0: 256, 1: 128, 2: 64, 3: 32, 4: 192}
 
 
 def oracle_one(M):
@@ -41,7 +41,8 @@ def test_ragged_mixed_sizes_against_oracle():
     check_against_oracle(mats, rb.results(), rb.info.cpu().numpy()[: rb.count], "ragged")
 
 
-@pytest.mark.parametrize("team,n", [(0, 64), (0, 41), (0, 33), (1, 32), (1, 19), (2, 16), (2, 5), (3, 16), (3, 3)])
+@pytest.mark.parametrize("team,n", [(0, 64), (0, 41), (0, 33), (1, 32), (1, 19), (2, 16), (2, 5), (3, 16), (3, 3),
+                                    (4, 48), (4, 40), (4, 33), (4, 20)])
 @pytest.mark.parametrize("leaf", [1, 2, 8])
 def test_ragged_equals_uniform_path_bitwise(team, n, leaf):
     """A ragged team runs the same per-matrix code as the uniform launch of the same shape."""
@@ -49,7 +50,7 @@ def test_ragged_equals_uniform_path_bitwise(team, n, leaf):
     t = B.bed_ragged_default_tuning()
     t.team[n], t.leaf[n] = team, leaf
     rb = B.RaggedBatch([n] * 37, tuning=t).load(list(A)).solve()
-    nmax = 64 if team == 0 else (32 if team == 1 else 16)
+    nmax = {0: 64, 1: 32, 2: 16, 3: 16, 4: 48}[team]
     Ad = torch.from_numpy(A).cuda()
     W = torch.empty(37, n, device="cuda")
     V = torch.empty(37, n, n, device="cuda")
