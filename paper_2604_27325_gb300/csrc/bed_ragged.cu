@@ -53,23 +53,54 @@ struct RaggedTune {
 };
 
 // Orders the matrices by (team type, n descending) with a counting sort; invalid sizes are flagged.
+// Each thread loads PER sizes at a time so that their global loads are in flight together; the bins of
+// each team type are scanned by one warp (two bins per lane).
 __global__ void __launch_bounds__(1024) ragged_order_kernel(const int32_t* __restrict__ ns, int64_t count,
                                                             const RaggedTune tune, RaggedHeader* __restrict__ hdr,
                                                             int32_t* __restrict__ order, int32_t* __restrict__ info)
 {
     constexpr int NK = kTeamTypes * kMaxN;  // key = type * 64 + (64 - n)
+    constexpr int PER = 8;
     __shared__ unsigned int hist[NK];
     __shared__ unsigned int offs[NK];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < NK; i += blockDim.x) hist[i] = 0;
+    __shared__ unsigned int tsum[kTeamTypes], tbase[kTeamTypes];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < NK; i += nt) hist[i] = 0;
     __syncthreads();
-    for (int64_t i = tid; i < count; i += blockDim.x) {
-        const int n = ns[i];
-        if (n < 1 || n > kMaxN) {
-            if (info) info[i] = BED_INFO_BAD_N;
-            continue;
+    for (int64_t base = 0; base < count; base += static_cast<int64_t>(nt) * PER) {
+        int v[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int64_t i = base + static_cast<int64_t>(k) * nt + tid;
+            v[k] = (i < count) ? ns[i] : 0;
         }
-        atomicAdd(&hist[tune.team[n] * kMaxN + (kMaxN - n)], 1u);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int64_t i = base + static_cast<int64_t>(k) * nt + tid;
+            if (i >= count) continue;
+            const int n = v[k];
+            if (n < 1 || n > kMaxN) {
+                if (info) info[i] = BED_INFO_BAD_N;
+                continue;
+            }
+            atomicAdd(&hist[tune.team[n] * kMaxN + (kMaxN - n)], 1u);
+        }
+    }
+    __syncthreads();
+    static_assert(kMaxN == 64, "two bins per lane");
+    if (warp < kTeamTypes) {
+        const int b0 = warp * kMaxN + 2 * lane;
+        const unsigned int h0 = hist[b0], h1 = hist[b0 + 1];
+        unsigned int x = h0 + h1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        offs[b0] = x - h0 - h1;  // relative to the start of the type
+        offs[b0 + 1] = x - h1;
+        if (lane == 31) tsum[warp] = x;
     }
     __syncthreads();
     if (tid == 0) {
@@ -77,13 +108,9 @@ __global__ void __launch_bounds__(1024) ragged_order_kernel(const int32_t* __res
         for (int t = 0; t < kTeamTypes; ++t) {
             hdr->mat_start[t] = acc;
             hdr->unit_start[t] = units;
-            unsigned int ct = 0;
-            for (int k = 0; k < kMaxN; ++k) {
-                offs[t * kMaxN + k] = acc + ct;
-                ct += hist[t * kMaxN + k];
-            }
-            acc += ct;
-            units += (ct + team_count(t) - 1) / team_count(t);
+            tbase[t] = acc;
+            acc += tsum[t];
+            units += (tsum[t] + team_count(t) - 1) / team_count(t);
         }
         hdr->mat_start[kTeamTypes] = acc;
         hdr->unit_start[kTeamTypes] = units;
@@ -91,11 +118,23 @@ __global__ void __launch_bounds__(1024) ragged_order_kernel(const int32_t* __res
         hdr->next_unit = 0;
     }
     __syncthreads();
-    for (int64_t i = tid; i < count; i += blockDim.x) {
-        const int n = ns[i];
-        if (n < 1 || n > kMaxN) continue;
-        const unsigned int p = atomicAdd(&offs[tune.team[n] * kMaxN + (kMaxN - n)], 1u);
-        order[p] = static_cast<int32_t>(i);
+    for (int i = tid; i < NK; i += nt) offs[i] += tbase[i / kMaxN];
+    __syncthreads();
+    for (int64_t base = 0; base < count; base += static_cast<int64_t>(nt) * PER) {
+        int v[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int64_t i = base + static_cast<int64_t>(k) * nt + tid;
+            v[k] = (i < count) ? ns[i] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int64_t i = base + static_cast<int64_t>(k) * nt + tid;
+            const int n = v[k];
+            if (i >= count || n < 1 || n > kMaxN) continue;
+            const unsigned int p = atomicAdd(&offs[tune.team[n] * kMaxN + (kMaxN - n)], 1u);
+            order[p] = static_cast<int32_t>(i);
+        }
     }
 }
 
