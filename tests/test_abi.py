@@ -144,3 +144,33 @@ def test_ragged_validation_before_launch():
     t = B.bed_ragged_default_tuning()
     t.leaf[5] = 9
     assert B.bed_eigh_ragged_f32(**{**args, "tuning": t}) == B.BED_ERR_INVALID_ARG
+
+
+def test_host_entry_points_validate_before_touching_the_device():
+    """Argument errors of the page-locked host entry points come back before any CUDA call."""
+    assert B.bed_eigh_f32_pinned(FAKE, FAKE, FAKE + 4096, None, 3, 65) == B.BED_ERR_UNSUPPORTED_N
+    assert B.bed_eigh_f32_pinned(FAKE, FAKE, FAKE + 4096, None, -1, 8) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32_pinned(FAKE, FAKE, FAKE + 4096, None, 3, 8, B.make_params(leaf_size=9)) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_f32_pinned(0, 0, 0, None, 0, 8) == B.BED_OK
+    L = B.lib()
+    assert L.bed_eigh_many_f32_pinned(-1, None, None, None, None, None, None, None, None, None, 0) == B.BED_ERR_INVALID_ARG
+    assert L.bed_eigh_many_f32_pinned(0, None, None, None, None, None, None, None, None, None, 0) == B.BED_OK
+    assert L.bed_eigh_many_f32_pinned(2, None, None, None, None, None, None, None, None, None, 1) == B.BED_ERR_INVALID_ARG
+    # sizes and counts are checked batch by batch before any buffer is looked at
+    args = ([FAKE], [FAKE], [FAKE + 4096], None, None, 0, [0])
+    assert B.bed_eigh_many_f32_pinned([65], [3], *args) == B.BED_ERR_UNSUPPORTED_N
+    assert B.bed_eigh_many_f32_pinned([8], [-2], *args) == B.BED_ERR_INVALID_ARG
+    assert B.bed_eigh_many_f32_pinned([8], [3], [FAKE], [FAKE], [FAKE + 4096], None,
+                                      B.make_params(merge_tensor_cores=3), 0, [0]) == B.BED_ERR_INVALID_ARG
+
+
+def test_async_api_has_no_cpu_path():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(B.BedError):
+        B.batched_eigh_many_async([torch.eye(4).unsqueeze(0)])
+    with pytest.raises(B.BedError):
+        B.batched_eigh_many([torch.eye(4).unsqueeze(0)])
+
