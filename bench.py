@@ -196,12 +196,12 @@ def shard(total: int, rank: int, world: int):
 # ------------------------------------------------------------------------------------------------ CPU legs
 
 
-def cpu_oracle_rate(inputs, budget_s: float, min_reps: int = 1):
-    """The FP64 oracle as it stands, on all host cores, over whole passes of the workload until
-    `budget_s` of wall time is spent. Returns (matrices/s, threads used, matrices solved)."""
+def cpu_oracle_rate(inputs, budget_s: float, min_reps: int = 1, nthreads: int | None = None):
+    """The FP64 oracle as it stands, on `nthreads` host cores (default all), over whole passes of the
+    workload until `budget_s` of wall time is spent. Returns (matrices/s, threads used, matrices solved)."""
     import oracle
 
-    nthreads = os.cpu_count() or 1
+    nthreads = nthreads or os.cpu_count() or 1
     used = 1
     done = 0
     t0 = time.perf_counter()
@@ -419,10 +419,19 @@ def run_ours(args, rank, world, local):
     per_step_units = BATCH * len(SIZES)
     value = per_step_units * world * K / (total_ms / 1e3)
 
-    # roofline of the dominant launch (n = 64)
+    # roofline of the dominant launch (n = 64). The FP32 peak is measured on this GPU by the FMA-chain
+    # probe (full occupancy, CUDA events, clocks sampled meanwhile); the nominal figure is kept beside it
     peaks = measured_peaks()
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz_max * 1e6 / 1e12  # TFLOP/s
+    fp32_nominal = props.multi_processor_count * 128 * 2 * sm_mhz_max * 1e6 / 1e12  # TFLOP/s
+    psamp = ClockSampler(local).start()
+    time.sleep(0.2)
+    t_p0 = time.time()
+    probe = B.fp32_fma_peak(dev)
+    t_p1 = time.time()
+    time.sleep(0.1)
+    pclk = ClockSampler.summarize(psamp.stop(), t_p0, t_p1)
+    fp32_peak = probe["tflops"]
     # the dominant kernel: the launch with the most algorithmic work (n = 64), timed on its own stream
     # while the other three run beside it
     dom = max(SIZES, key=lambda n: flops_per_matrix(n, kbar[n]))
@@ -456,30 +465,46 @@ def run_ours(args, rank, world, local):
     groups = {n: (torch.from_numpy(np.stack(ms)).to(dev), torch.empty(len(ms), n, device=dev),
                   torch.empty(len(ms), n, n, device=dev)) for n, ms in by_n.items()}
 
-    def per_size_step():
-        for n, (a, w, v) in groups.items():
-            st = B.bed_eigh_f32(a.data_ptr(), w.data_ptr(), v.data_ptr(), None, a.shape[0], n, None, sp)
+    # the fair reference: the same per-size launches the headline step uses, each distinct n on its own
+    # stream forked from and joined to the origin, largest n first, the whole step captured as one CUDA
+    # graph and replayed
+    g_side = {n: torch.cuda.Stream(dev) for n in groups}
+
+    def per_size_step(origin):
+        fork = torch.cuda.Event()
+        fork.record(origin)
+        for n in sorted(groups, reverse=True):
+            a, w, v = groups[n]
+            g_side[n].wait_event(fork)
+            st = B.bed_eigh_f32(a.data_ptr(), w.data_ptr(), v.data_ptr(), None, a.shape[0], n, None,
+                                g_side[n].cuda_stream)
             if st != B.BED_OK:
                 raise B.BedError(B.bed_status_string(st))
+            j = torch.cuda.Event()
+            j.record(g_side[n])
+            origin.wait_event(j)
 
-    for i in range(args.warmup):
-        per_size_step()
+    per_size_step(stream)
     torch.cuda.synchronize(dev)
-    ps_ms = []
-    for s_ in range(K):
-        flush.fill_(float(s_))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        per_size_step()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ps_ms.append(e0.elapsed_time(e1))
+    ps_graph = torch.cuda.CUDAGraph()
+    cap.wait_stream(stream)
+    with torch.cuda.graph(ps_graph, stream=cap):
+        per_size_step(cap)
+    torch.cuda.synchronize(dev)
+
+    class _Replay:
+        def replay(self):
+            ps_graph.replay()
+
+    ps_ms = timed_replays(_Replay(), flush, args.warmup, K, stream)
     ragged = {
         "workload": f"ragged: {RAGGED_COUNT} FP32 matrices, n ~ U{{4..64}}, even index gapped known spectrum, "
                     "odd index covariance",
         "persistent_graph": RAGGED_COUNT * world * K / (max_over_ranks(sum(rg_ms), world) / 1e3),
         "per_size_launches": RAGGED_COUNT * world * K / (max_over_ranks(sum(ps_ms), world) / 1e3),
         "per_size_launch_count": len(groups),
+        "per_size_how": "one launch per distinct n, each on its own stream (fork/join), the step replayed "
+                        "as one CUDA graph",
         "unit": "matrices/s",
     }
     ragged["speedup_vs_per_size"] = ragged["persistent_graph"] / ragged["per_size_launches"]
@@ -533,23 +558,70 @@ def run_ours(args, rank, world, local):
     if args.serving_seconds > 0:
         pool = serve.request_pool()
         keep = ("p50_ms", "p99_ms", "mean_ms", "matrices_per_s", "requests", "offered_requests", "launches",
-                "peak_device_bytes")
+                "requests_per_launch", "achieved_submit_rate", "peak_device_bytes")
+
+        def load(mode, rate, seconds):
+            srv = serve.NativeServer(budget_bytes=4 << 30, tuning=tuning if mode == "batch" else None, mode=mode)
+            try:
+                out = serve.run_load_native(srv, rate=rate, seconds=seconds, pool=pool)
+            finally:
+                srv.close()
+            return {k: out.get(k) for k in keep}
+
         serving = {
             "workload": "Poisson arrivals; request = b ~ U{1..256} FP32 matrices of one n ~ U{8..64} (gapped known "
-                        "spectra and covariances); 4 GB device budget; latency = submit to results in host memory",
+                        "spectra and covariances, page-locked); 4 GB device budget; latency = submit to results "
+                        "in host memory",
+            "servers": "native request loop (bed_server_*), zero-copy data path: continuous batching over the "
+                       "ragged kernel on 3 streams vs FIFO with one uniform-size launch per request",
             "seconds": args.serving_seconds,
         }
-        serving["servers"] = ("native request loop (bed_server_*): continuous batching over the ragged "
-                              "kernel on 3 streams vs FIFO with one uniform-size launch per request")
-        for rate in (args.serving_rate, 4 * args.serving_rate):
-            srv = serve.NativeServer(budget_bytes=4 << 30, tuning=tuning)
-            ours_s = serve.run_load_native(srv, rate=rate, seconds=args.serving_seconds, pool=pool)
-            srv.close()
-            q = serve.NativeServer(budget_bytes=4 << 30, mode="fifo")
-            base_s = serve.run_load_native(q, rate=rate, seconds=args.serving_seconds, pool=pool)
-            q.close()
-            serving[f"rate_{rate:.0f}"] = {"continuous_batching": {k: ours_s.get(k) for k in keep},
-                                           "fifo_per_request_launches": {k: base_s.get(k) for k in keep}}
+        serving[f"rate_{args.serving_rate:.0f}"] = {
+            "continuous_batching": load("batch", args.serving_rate, args.serving_seconds),
+            "fifo_per_request_launches": load("fifo", args.serving_rate, args.serving_seconds)}
+        # saturation sweep: short runs at rising offered load, until FIFO falls behind
+        sweep = {}
+        fifo_done = False
+        for rate in args.sweep_rates:
+            cb = load("batch", rate, args.sweep_seconds)
+            row = {"offered_matrices_per_s": rate * 128.5, "continuous_batching": cb}
+            if not fifo_done:
+                ff = load("fifo", rate, args.sweep_seconds)
+                row["fifo_per_request_launches"] = ff
+                fifo_done = (ff["matrices_per_s"] or 0) < 0.9 * rate * 128.5
+            sweep[f"rate_{rate:.0f}"] = row
+        serving["sweep"] = sweep
+        serving["sweep_seconds"] = args.sweep_seconds
+
+    # context: torch.linalg.eigh (cuSOLVER) on the same four batches on the same GPU, CUDA events, no graph
+    torch_eigh = None
+    if not args.no_torch_eigh:
+        t_one = {}
+        for n in SIZES:
+            for _ in range(3):
+                torch.linalg.eigh(Ad[n])
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.linalg.eigh(Ad[n])
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t_one[n] = e0.elapsed_time(e1)
+        reps = int(max(3, min(K, 8000.0 / max(sum(t_one.values()), 1e-3))))
+        t_tot = 0.0
+        for r_ in range(reps):
+            flush.fill_(float(r_))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for n in SIZES:
+                torch.linalg.eigh(Ad[n])
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t_tot += e0.elapsed_time(e1)
+        torch_eigh = {"value": per_step_units * reps / (t_tot / 1e3), "unit": "matrices/s", "reps": reps,
+                      "per_n_ms": {str(n): t_one[n] for n in SIZES},
+                      "what": "torch.linalg.eigh on the same 4 x 512 device tensors, one call per n, CUDA events, "
+                              "L2 flushed before each step"}
 
     # end to end through the public API with host buffers: every step reads its inputs from and writes
     # its results to page-locked host memory. Pipelined: step s + 1 is submitted before waiting for the
@@ -609,7 +681,12 @@ def run_ours(args, rank, world, local):
                      "kernel": f"eigh_kernel n={dom} batch={BATCH} (duration on its stream, concurrent with "
                                f"the other sizes)",
                      "step_achieved": step_flops / (ms_per_step / 1e3) / 1e12,
-                     "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_mhz_max:.0f} MHz",
+                     "peak_source": (f"measured: FMA-chain probe (bed_fma_peak_launch, {probe['blocks']} x "
+                                     f"{probe['threads']} threads x {probe['chains']} chains), best of 5, SM clock "
+                                     f"median {pclk['sm_mhz']} MHz during it"),
+                     "peak_nominal": fp32_nominal,
+                     "peak_nominal_source": f"{props.multi_processor_count} SMs x 128 lanes x 2 x {sm_mhz_max:.0f} MHz",
+                     "frac_of_nominal": achieved / fp32_nominal,
                      "hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm / hbm_peak,
                              "frac_of_8tbs": hbm / 8000.0}},
         "e2e": {"value": per_step_units * world * K / e2e_s, "unit": "matrices/s",
@@ -620,11 +697,41 @@ def run_ours(args, rank, world, local):
         "gpu_launches": K * (2 if uniform_via_ragged > value else len(SIZES)),
         "clocks": clocks,
     }
+    if torch_eigh is not None:
+        line["context"] = {"torch_linalg_eigh": torch_eigh}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, used, done = cpu_oracle_rate(inputs, budget_s=args.cpu_budget)
+        r1, used1, done1 = cpu_oracle_rate(inputs, budget_s=args.cpu_budget, nthreads=1)
         line["cpu_baseline"] = {"value": rate, "unit": "matrices/s", "cores": used, "kind": "oracle",
                                 "sample": f"whole passes of the workload ({done} matrices, about "
-                                          f"{args.cpu_budget:.0f} s wall on {used} threads)"}
+                                          f"{args.cpu_budget:.0f} s wall on {used} threads)",
+                                "one_core": {"value": r1, "unit": "matrices/s", "cores": used1,
+                                             "sample": f"whole passes ({done1} matrices, about "
+                                                       f"{args.cpu_budget:.0f} s on 1 thread)"}}
+    # the secondary results once more, compact and last, so that a truncated tail of the line still
+    # shows them
+    summ = {"per_size_Mps": value / 1e6, "ragged_path_on_uniform_Mps": uniform_via_ragged / 1e6,
+            "ragged8192_persistent_Mps": ragged["persistent_graph"] / 1e6,
+            "ragged8192_per_size_graph_Mps": ragged["per_size_launches"] / 1e6,
+            "fp32_peak_measured_tflops": fp32_peak, "frac": achieved / fp32_peak,
+            "e2e_Mps": line["e2e"]["value"] / 1e6}
+    if torch_eigh is not None:
+        summ["torch_eigh_Mps"] = torch_eigh["value"] / 1e6
+    if "cpu_baseline" in line:
+        summ["oracle_all_cores_per_s"] = line["cpu_baseline"]["value"]
+        summ["oracle_one_core_per_s"] = line["cpu_baseline"]["one_core"]["value"]
+    if serving is not None:
+        r0 = serving[f"rate_{args.serving_rate:.0f}"]
+        summ["serve_2000"] = {k: [round(r0[m][k], 4) if r0[m].get(k) is not None else None
+                                  for m in ("continuous_batching", "fifo_per_request_launches")]
+                              for k in ("p50_ms", "p99_ms", "matrices_per_s")}
+        summ["serve_sweep_Mps_cb_fifo_p99ms"] = {
+            k: [round((v["continuous_batching"]["matrices_per_s"] or 0) / 1e6, 3),
+                round((v.get("fifo_per_request_launches", {}).get("matrices_per_s") or 0) / 1e6, 3),
+                round(v["continuous_batching"]["p99_ms"] or 0, 3),
+                round(v.get("fifo_per_request_launches", {}).get("p99_ms") or 0, 3)]
+            for k, v in serving["sweep"].items()}
+    line["summary"] = summ
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -638,8 +745,11 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=5.0)
-    ap.add_argument("--serving-seconds", type=float, default=8.0)
+    ap.add_argument("--serving-seconds", type=float, default=60.0)
     ap.add_argument("--serving-rate", type=float, default=2000.0)
+    ap.add_argument("--sweep-rates", type=float, nargs="*", default=[2000.0, 8000.0, 16000.0, 32000.0])
+    ap.add_argument("--sweep-seconds", type=float, default=3.0)
+    ap.add_argument("--no-torch-eigh", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

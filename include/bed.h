@@ -5,7 +5,8 @@
  * Method: Y. Song, "A Short Note on Batch-efficient Divide-and-Conquer Algorithm for
  * EigenDecomposition" (arXiv 2604.27325), Sec. 2. Each matrix is reduced to tridiagonal form by
  * Householder reflections (Sec. 2 defers this stage to the authors' earlier work), torn into
- * rank-one-coupled blocks (Sec. 2.1, Eq. (1)-(3)) down to 2x2 leaves (Sec. 2.2), merged back through
+ * rank-one-coupled blocks (Sec. 2.1, Eq. (1)-(3)) down to leaves of at most 8 rows (Sec. 2.2: 1x1 and
+ * 2x2 leaves in closed form, larger ones by the implicit QL iteration), merged back through
  * the secular equation (Sec. 2.3, Eq. (4)-(22)) with Gu-Eisenstat eigenvectors (Eq. (23)-(25)), and
  * back-transformed. One launch runs the whole path for every matrix of the batch; each matrix lives
  * in one thread block's shared memory.
@@ -50,7 +51,9 @@ enum {
     BED_INFO_OK = 0,
     BED_INFO_NOT_CONVERGED = 1, /* a secular root hit the iteration cap; its last iterate is kept */
     BED_INFO_NONFINITE = 2,     /* A[b] held a NaN or an infinity: W[b] and V[b] are set to NaN */
-    BED_INFO_TIMEOUT = 4,       /* the staging copy of A[b] did not complete in time: W[b], V[b] NaN */
+    BED_INFO_TIMEOUT = 4,       /* the staging copy of A[b] did not complete within stage_wait_us: W[b], V[b]
+                                   NaN; the team goes on once the copy has landed (a second wait of at most
+                                   2 s), and stops taking matrices if it never does */
     BED_INFO_BAD_N = 8          /* ragged batches: ns[b] outside [1, 64]; the matrix was skipped */
 };
 
@@ -81,6 +84,10 @@ typedef struct {
                                 tiles than the registers hold, 2*nmax teams, the ragged kernel and the
                                 server use the FP32 products. Results agree with the FP32 path to the
                                 same tolerance, not bitwise. */
+    int stage_wait_us;       /* limit in microseconds of a team's wait for the bulk copy that stages a matrix
+                                in shared memory, 0..60,000,000 (default 2,000,000); a matrix whose copy has
+                                not landed by then gets BED_INFO_TIMEOUT. 0 gives up without waiting, which
+                                exercises that path deterministically (the copy is still drained). */
 } bed_params;
 
 /* Fills *p with the defaults listed above. */
@@ -238,9 +245,11 @@ bed_status bed_eigh_ragged_f32(const float* A, const int64_t* offsets, const int
  *     GPU (different streams without ordering between them) race on the scratch and give undefined
  *     results; order such calls or use bed_eigh_ragged_f32 with separate workspaces.
  *   - It calls no allocation routine. Arguments otherwise as for bed_eigh_ragged_f32.
+ *   - The looked-up address and the device setup are cached per device for the life of the process;
+ *     after cudaDeviceReset the library must be reloaded before it is used on that device again.
  */
 #define BED_NOALLOC_MAX_COUNT 65536
-#define BED_NOALLOC_SCRATCH_BYTES (64 + 4 * BED_NOALLOC_MAX_COUNT)
+#define BED_NOALLOC_SCRATCH_BYTES ((64 + 4 * BED_NOALLOC_MAX_COUNT + 255) / 256 * 256)
 bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count,
                                        float* W, const int64_t* w_offsets, float* V, int32_t* info,
                                        const bed_params* p, const bed_ragged_tuning* tuning,
@@ -260,18 +269,23 @@ bed_status bed_eigh_backward_f32(const float* W, const float* V, const float* gW
                                  int64_t batch, int n, float gap_eps, cudaStream_t stream);
 
 /*
- * Request loop (continuous batching) for serving eigendecompositions on the current device.
+ * Request loop (continuous batching) for serving eigendecompositions on the current device (no
+ * counterpart in the paper, whose introduction motivates the method by training and inference).
  * A request is b matrices of one size n in host memory (row-major, lower triangle read). The server
- * admits requests in arrival order while their device memory (input, eigenvectors, eigenvalues) fits
- * `device_budget_bytes` and their results fit `host_result_bytes` of pinned host memory; everything
- * admitted since the previous launch is solved by one ragged launch (bed_eigh_ragged_f32) on a free
- * one of `streams` streams, so requests that arrive while others run are admitted as memory and
- * streams free up and their work overlaps on the device. A launch that carries a single request uses the
- * uniform kernel with the ragged kernel's team shape and leaf size for its n, so a request's results are
- * the same whether or not it shared a launch. mode 1 instead runs one uniform-size launch (default
- * parameters) per request, first come first served, on one stream (the plain per-request baseline).
- * The server allocates its device and pinned host memory once, in bed_server_create, and owns two
- * threads; every entry point below is thread-safe.
+ * admits requests in arrival order while their results fit `host_result_bytes` of pinned host memory
+ * and whatever they stage in the device arena fits `device_budget_bytes`; everything admitted since
+ * the previous launch is solved by one ragged launch (the persistent kernel of bed_eigh_ragged_f32) on
+ * a free one of `streams` streams, so requests that arrive while others run are admitted as slots and
+ * memory free up and their work overlaps on the device. A launch that carries a single request uses
+ * the uniform kernel with the ragged kernel's team shape and leaf size for its n, so a request's results
+ * are the same whether or not it shared a launch. With zero_copy = 1 (default) a page-locked input is
+ * read by the kernels in place and the results are written straight into the pinned result memory
+ * (inputs that are not page-locked are copied into the device arena first); with zero_copy = 0 inputs
+ * and results pass through the device arena with copies. A completion thread polls every launch in
+ * flight and retires each as soon as it is done. mode 1 instead runs one uniform-size launch (default
+ * parameters) per request, first come first served, on one stream (the plain per-request baseline,
+ * with the same data path). The server allocates its device and pinned host memory once, in
+ * bed_server_create, and owns two threads; every entry point below is thread-safe.
  */
 typedef struct bed_server bed_server;
 
@@ -281,6 +295,8 @@ typedef struct {
     int streams;                /* launches that may be in flight at once (default 3; 1 in mode 1) */
     int max_launch_matrices;    /* cap on the matrices of one launch (default 16384) */
     int mode;                   /* 0: continuous batching (default); 1: one launch per request */
+    int zero_copy;              /* 1 (default): page-locked inputs read in place, results written in place;
+                                   0: inputs and results copied through the device arena */
 } bed_server_config;
 
 typedef struct {
@@ -298,8 +314,9 @@ bed_status bed_server_create(const bed_server_config* cfg, const bed_params* p, 
                              bed_server** out);
 
 /* Queues b x n x n FP32 matrices at A_host (host memory that must stay unchanged until the request
- * completes; pinned memory lets the copy run asynchronously). *request_id identifies it. A request that
- * alone exceeds the budgets is refused with BED_ERR_TOO_LARGE (it still gets an id to release). */
+ * completes; page-locked memory is read in place by the kernels under zero_copy, other memory is copied
+ * to the device arena). *request_id identifies it. A request that alone exceeds the budgets or has more
+ * than max_launch_matrices matrices is refused with BED_ERR_TOO_LARGE (it still gets an id to release). */
 bed_status bed_server_submit(bed_server* s, const float* A_host, int32_t b, int32_t n, int64_t* request_id);
 
 /* Waits up to timeout_s seconds (< 0: without limit) for a request; on BED_OK, *V ([b][n][n], columns
@@ -317,6 +334,16 @@ bed_status bed_server_reset_stats(bed_server* s);
 
 /* Stops the threads after the queued requests are launched, waits for the device, frees everything. */
 void bed_server_destroy(bed_server* s);
+
+/*
+ * FP32 FMA throughput probe (no counterpart in the paper: it measures the denominator of the
+ * eigensolver's FP32 ALU roofline). Launches `blocks` x `threads` threads (threads a multiple of 32,
+ * at most 256), each running bed_fma_peak_chains() independent FMA chains for `iters` rounds, and
+ * writes one float per thread to out [blocks * threads] (device memory) so the work is kept. The caller
+ * times the launch: it performs 2 * bed_fma_peak_chains() * iters * blocks * threads FP32 FLOPs.
+ */
+int bed_fma_peak_chains(void);
+bed_status bed_fma_peak_launch(float* out, int blocks, int threads, int iters, cudaStream_t stream);
 
 /* Largest supported n (64). */
 int bed_max_n(void);

@@ -41,6 +41,7 @@ class bed_params(C.Structure):
         ("threads_per_matrix", C.c_int),
         ("retire_by_vote", C.c_int),
         ("merge_tensor_cores", C.c_int),
+        ("stage_wait_us", C.c_int),
     ]
 
 
@@ -59,7 +60,7 @@ class bed_ragged_tuning(C.Structure):
 
 class bed_server_config(C.Structure):
     _fields_ = [("device_budget_bytes", C.c_size_t), ("host_result_bytes", C.c_size_t), ("streams", C.c_int),
-                ("max_launch_matrices", C.c_int), ("mode", C.c_int)]
+                ("max_launch_matrices", C.c_int), ("mode", C.c_int), ("zero_copy", C.c_int)]
 
 
 class bed_server_stats(C.Structure):
@@ -88,6 +89,8 @@ EXPORTED = [
     "bed_server_get_stats",
     "bed_server_reset_stats",
     "bed_server_destroy",
+    "bed_fma_peak_chains",
+    "bed_fma_peak_launch",
     "bed_max_n",
     "bed_status_string",
     "bed_last_cuda_error",
@@ -119,6 +122,10 @@ def lib() -> C.CDLL:
             L.bed_eigh_many_f32_pinned.argtypes = [C.c_int, vp, vp, vp, vp, vp, vp, C.POINTER(bed_params), vp, vp,
                                                    C.c_int]
             L.bed_eigh_many_f32_pinned.restype = C.c_int
+            L.bed_fma_peak_chains.argtypes = []
+            L.bed_fma_peak_chains.restype = C.c_int
+            L.bed_fma_peak_launch.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
+            L.bed_fma_peak_launch.restype = C.c_int
             L.bed_max_n.argtypes = []
             L.bed_max_n.restype = C.c_int
             L.bed_status_string.argtypes = [C.c_int]
@@ -292,6 +299,36 @@ def bed_server_destroy(h) -> None:
 
 def bed_max_n() -> int:
     return lib().bed_max_n()
+
+
+def bed_fma_peak_chains() -> int:
+    return lib().bed_fma_peak_chains()
+
+
+def bed_fma_peak_launch(out, blocks: int, threads: int, iters: int, stream=None) -> int:
+    return lib().bed_fma_peak_launch(out, blocks, threads, iters, stream)
+
+
+def fp32_fma_peak(device=None, reps: int = 5, iters: int = 200000) -> dict:
+    """Measured FP32 FMA throughput of the device (TFLOP/s, best of ``reps`` CUDA-event-timed launches
+    of the FMA-chain probe at full occupancy: 8 blocks of 256 threads per SM)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    _check(bed_fma_peak_launch(out.data_ptr(), blocks, threads, 1000, s.cuda_stream))
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        _check(bed_fma_peak_launch(out.data_ptr(), blocks, threads, iters, s.cuda_stream))
+        e1.record(s)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        flops = 2.0 * bed_fma_peak_chains() * iters * blocks * threads
+        best = max(best, flops / (ms / 1e3) / 1e12)
+    return {"tflops": best, "blocks": blocks, "threads": threads, "iters": iters, "chains": bed_fma_peak_chains()}
 
 
 def bed_status_string(s: int) -> str:

@@ -17,7 +17,7 @@ LIB = os.path.join(OUT, "libbed.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["bed_api.cu", "bed_kernel_16.cu", "bed_kernel_32.cu", "bed_kernel_48.cu", "bed_kernel_64.cu", "bed_ragged.cu",
-           "bed_backward.cu", "bed_serve.cu"]
+           "bed_backward.cu", "bed_serve.cu", "bed_peak.cu"]
 HEADERS = ["bed_internal.h", "bed_kernel.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]

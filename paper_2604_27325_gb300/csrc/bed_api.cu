@@ -36,14 +36,14 @@ void split(int lo, int hi, int depth, int leaf, std::vector<MergeRec>& merges, s
 
 thread_local char g_last_cuda_error[256] = "";
 
+}  // namespace
+
 bed_status cuda_fail(cudaError_t e)
 {
     std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s: %s", cudaGetErrorName(e),
                   cudaGetErrorString(e));
     return BED_ERR_CUDA;
 }
-
-}  // namespace
 
 bool build_plan(int n, int leaf_size, Plan* P)
 {
@@ -118,8 +118,6 @@ cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int
     return cudaErrorInvalidValue;
 }
 
-namespace {
-
 // Validates the parameters shared by every entry point and derives the kernel constants.
 bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
 {
@@ -134,6 +132,7 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
     if (!(prm->deflation_tol_scale >= 1.f && prm->deflation_tol_scale <= 1e6f)) return false;
     if (prm->retire_by_vote != 0 && prm->retire_by_vote != 1) return false;
     if (prm->merge_tensor_cores != 0 && prm->merge_tensor_cores != 1) return false;
+    if (prm->stage_wait_us < 0 || prm->stage_wait_us > 60000000) return false;
     kp->k_ms = prm->k_multisection;
     kp->max_sec = prm->max_section_iters;
     kp->max_halley = prm->max_halley_iters;
@@ -142,8 +141,11 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
     kp->defl_c = prm->deflation_tol_scale;
     kp->retire = prm->retire_by_vote;
     kp->merge_tc = prm->merge_tensor_cores;
+    kp->stage_wait_ns = 1000ull * static_cast<unsigned long long>(prm->stage_wait_us);
     return true;
 }
+
+namespace {
 
 // Team shape: nmax rows of tiles, G lanes per row; the smallest nmax that holds n unless the caller
 // asks for a thread count, which then selects the smallest (nmax >= n, G) with G * nmax equal to it.
@@ -168,6 +170,8 @@ bool team_shape(int n, const bed_params& prm, int* nmax_out, int* g_out)
     *g_out = g;
     return true;
 }
+
+}  // namespace
 
 bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
                        const bed_params* p, bed_counters* counters, cudaStream_t stream, bool host_mapped)
@@ -196,6 +200,8 @@ bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_
     if (e != cudaSuccess) return cuda_fail(e);
     return BED_OK;
 }
+
+namespace {
 
 bool tuning_valid(const bed_ragged_tuning& t)
 {
@@ -270,6 +276,7 @@ void bed_default_params(bed_params* p)
     p->threads_per_matrix = 0;
     p->retire_by_vote = 1;
     p->merge_tensor_cores = 0;
+    p->stage_wait_us = 2000000;
 }
 
 bed_status bed_eigh_f32(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
@@ -331,7 +338,9 @@ bed_status bed_eigh_f32_host(const float* A_host, float* W_host, float* V_host, 
     return BED_OK;
 }
 
-namespace {
+}  // extern "C"
+
+namespace bed {
 
 // Device address of the page-locked host range [p, p + bytes) in the current context, or nullptr when
 // any part of it is not page-locked memory mapped into the device's address space. Both ends must lie
@@ -353,7 +362,9 @@ const void* mapped_range(const void* p, size_t bytes)
     return a.devicePointer;
 }
 
-}  // namespace
+}  // namespace bed
+
+extern "C" {
 
 bed_status bed_eigh_f32_pinned(const float* A_host, float* W_host, float* V_host, int32_t* info_host,
                                int64_t batch, int n, const bed_params* p, cudaStream_t stream)
@@ -367,12 +378,12 @@ bed_status bed_eigh_f32_pinned(const float* A_host, float* W_host, float* V_host
     }
     if (batch == 0) return BED_OK;
     const size_t nn = static_cast<size_t>(n) * n, b = static_cast<size_t>(batch);
-    const float* A = static_cast<const float*>(mapped_range(A_host, b * nn * sizeof(float)));
-    float* W = static_cast<float*>(const_cast<void*>(mapped_range(W_host, b * n * sizeof(float))));
-    float* V = static_cast<float*>(const_cast<void*>(mapped_range(V_host, b * nn * sizeof(float))));
+    const float* A = static_cast<const float*>(bed::mapped_range(A_host, b * nn * sizeof(float)));
+    float* W = static_cast<float*>(const_cast<void*>(bed::mapped_range(W_host, b * n * sizeof(float))));
+    float* V = static_cast<float*>(const_cast<void*>(bed::mapped_range(V_host, b * nn * sizeof(float))));
     int32_t* info = nullptr;
     if (info_host) {
-        info = static_cast<int32_t*>(const_cast<void*>(mapped_range(info_host, b * sizeof(int32_t))));
+        info = static_cast<int32_t*>(const_cast<void*>(bed::mapped_range(info_host, b * sizeof(int32_t))));
         if (!info) return BED_ERR_INVALID_ARG;
     }
     if (!A || !W || !V) return BED_ERR_INVALID_ARG;
@@ -406,12 +417,12 @@ bed_status bed_eigh_many_f32_pinned(int count, const int* ns, const int64_t* bat
         if (batches[k] == 0) continue;
         const size_t nn = static_cast<size_t>(n) * n, b = static_cast<size_t>(batches[k]);
         Dev& d = dp[k];
-        d.A = static_cast<const float*>(mapped_range(A_host[k], b * nn * sizeof(float)));
-        d.W = static_cast<float*>(const_cast<void*>(mapped_range(W_host[k], b * n * sizeof(float))));
-        d.V = static_cast<float*>(const_cast<void*>(mapped_range(V_host[k], b * nn * sizeof(float))));
+        d.A = static_cast<const float*>(bed::mapped_range(A_host[k], b * nn * sizeof(float)));
+        d.W = static_cast<float*>(const_cast<void*>(bed::mapped_range(W_host[k], b * n * sizeof(float))));
+        d.V = static_cast<float*>(const_cast<void*>(bed::mapped_range(V_host[k], b * nn * sizeof(float))));
         d.info = nullptr;
         if (info_host && info_host[k]) {
-            d.info = static_cast<int32_t*>(const_cast<void*>(mapped_range(info_host[k], b * sizeof(int32_t))));
+            d.info = static_cast<int32_t*>(const_cast<void*>(bed::mapped_range(info_host[k], b * sizeof(int32_t))));
             if (!d.info) return BED_ERR_INVALID_ARG;
         }
         if (!d.A || !d.W || !d.V || d.A == d.V) return BED_ERR_INVALID_ARG;

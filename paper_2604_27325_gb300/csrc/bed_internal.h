@@ -38,6 +38,7 @@ struct KParams {
     float defl_c;     // deflation tolerance scale
     int retire;       // warp-vote retirement of converged roots
     int merge_tc;     // merge products on the tensor cores (split-3xTF32)
+    unsigned long long stage_wait_ns;  // limit of the wait for a matrix's staging copy
 };
 
 bool build_plan(int n, int leaf_size, Plan* P);
@@ -56,6 +57,36 @@ cudaError_t launch_backward(const float* W, const float* V, const float* gW, con
                             int64_t batch, int n, float gap_eps, cudaStream_t stream);
 // Device address of the allocation-free entry point's scratch on the current device (looked up once).
 cudaError_t noalloc_scratch(void** ptr);
+
+// One uniform-size launch after full argument validation (the body of bed_eigh_f32); host_mapped: A, W,
+// V, info may be device-visible addresses of page-locked host memory, read and written with plain
+// loads and stores (no bulk-copy staging).
+bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,
+                       const bed_params* p, bed_counters* counters, cudaStream_t stream, bool host_mapped);
+
+// Device address of the page-locked host range [p, p + bytes) in the current context, or nullptr.
+const void* mapped_range(const void* p, size_t bytes);
+
+// Records a CUDA error for bed_last_cuda_error() and returns BED_ERR_CUDA.
+bed_status cuda_fail(cudaError_t e);
+
+// Addresses of one matrix of a ragged launch in descriptor form (any mix of device memory and
+// device-visible page-locked host memory).
+struct MatDesc {
+    const float* A;  // n x n input, row-major, lower triangle read
+    float* W;        // n eigenvalues
+    float* V;        // n x n eigenvectors (columns)
+    int32_t* info;   // one flag word (may be null)
+};
+
+// Ragged launch over descriptors: matrix b has size ns[b] and the addresses desc[b]; desc and ns may
+// themselves be device-visible page-locked host memory. Inputs are read with plain loads.
+cudaError_t launch_ragged_desc(const MatDesc* desc, const int32_t* ns, int64_t count,
+                               const bed_ragged_tuning& tuning, const KParams& kp, void* workspace,
+                               cudaStream_t stream);
+
+// Validates bed_params and derives the kernel constants (false: out of range).
+bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp);
 
 // TC: the merge products on the tensor cores (split-3xTF32), instantiated for G = 4 teams only.
 template <int NMAX, int G, bool TC = false>

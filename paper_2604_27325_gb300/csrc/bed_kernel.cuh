@@ -229,11 +229,13 @@ __device__ __forceinline__ uint64_t global_timer_ns()
     return t;
 }
 
-// Waits for phase `parity` of the mbarrier; gives up after `limit_ns` and returns false.
+// Waits for phase `parity` of the mbarrier; gives up once `limit_ns` have passed (checked before every
+// poll, so a limit of 0 gives up without polling) and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns)
 {
     const uint64_t t0 = global_timer_ns();
     for (;;) {
+        if (global_timer_ns() - t0 >= limit_ns) return false;
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -243,9 +245,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (global_timer_ns() - t0 > limit_ns) return false;
     }
 }
+
+// Internal flag of S.info (never stored): a staging copy that timed out was still in flight after the
+// second, draining wait, so the mbarrier phase is unknown and the team must stop.
+constexpr int kInfoUndrained = 1 << 16;
+constexpr uint64_t kDrainWaitNs = 2000000000ull;
 
 // ---------------------------------------------------------------------------------------------
 // a3 for leaves of 3..8 rows: implicit QL iteration with Wilkinson shifts (the small-block solver the
@@ -442,25 +448,27 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, sa = 0.f;
         if (!done) {
             const float dorg = dz[o].x;
-            // two poles per pass with separate partial sums (independent dependency chains)
+            // four poles per pass (their loads and reciprocals in flight together), accumulated in two
+            // independent partial sums; then one pole at a time for the remainder
             if (deriv) {
                 float s0b = 0.f, s1b = 0.f, s2b = 0.f, sab = 0.f;
                 int j = sub;
-                for (; j + G < K; j += 2 * G) {
-                    const float2 pa = dz[j], pb = dz[j + G];
+                for (; j + 3 * G < K; j += 4 * G) {
+                    const float2 pa = dz[j], pb = dz[j + G], pc = dz[j + 2 * G], pd = dz[j + 3 * G];
                     const float ia = rcp_approx((pa.x - dorg) - h), ib = rcp_approx((pb.x - dorg) - h);
-                    const float ta = pa.y * ia, tb = pb.y * ib;
-                    const float tia = ta * ia, tib = tb * ib;
-                    s0 += ta;
-                    s0b += tb;
-                    s1 += tia;
-                    s1b += tib;
-                    s2 = fmaf(tia, ia, s2);
-                    s2b = fmaf(tib, ib, s2b);
-                    sa += fabsf(ta);
-                    sab += fabsf(tb);
+                    const float ic = rcp_approx((pc.x - dorg) - h), id = rcp_approx((pd.x - dorg) - h);
+                    const float ta = pa.y * ia, tb = pb.y * ib, tc = pc.y * ic, td = pd.y * id;
+                    const float tia = ta * ia, tib = tb * ib, tic = tc * ic, tid = td * id;
+                    s0 += ta + tc;
+                    s0b += tb + td;
+                    s1 += tia + tic;
+                    s1b += tib + tid;
+                    s2 = fmaf(tia, ia, fmaf(tic, ic, s2));
+                    s2b = fmaf(tib, ib, fmaf(tid, id, s2b));
+                    sa += fabsf(ta) + fabsf(tc);
+                    sab += fabsf(tb) + fabsf(td);
                 }
-                if (j < K) {
+                for (; j < K; j += G) {
                     const float2 pa = dz[j];
                     const float ia = rcp_approx((pa.x - dorg) - h);
                     const float ta = pa.y * ia;
@@ -475,18 +483,20 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
                 s2 += s2b;
                 sa += sab;
             } else {
-                float s0b = 0.f;
+                float s0b = 0.f, s0c = 0.f, s0d = 0.f;
                 int j = sub;
-                for (; j + G < K; j += 2 * G) {
-                    const float2 pa = dz[j], pb = dz[j + G];
+                for (; j + 3 * G < K; j += 4 * G) {
+                    const float2 pa = dz[j], pb = dz[j + G], pc = dz[j + 2 * G], pd = dz[j + 3 * G];
                     s0 = fmaf(pa.y, rcp_approx((pa.x - dorg) - h), s0);
                     s0b = fmaf(pb.y, rcp_approx((pb.x - dorg) - h), s0b);
+                    s0c = fmaf(pc.y, rcp_approx((pc.x - dorg) - h), s0c);
+                    s0d = fmaf(pd.y, rcp_approx((pd.x - dorg) - h), s0d);
                 }
-                if (j < K) {
+                for (; j < K; j += G) {
                     const float2 pa = dz[j];
                     s0 = fmaf(pa.y, rcp_approx((pa.x - dorg) - h), s0);
                 }
-                s0 += s0b;
+                s0 = (s0 + s0b) + (s0c + s0d);
             }
         }
         s0 = gsum<G>(s0);
@@ -690,6 +700,7 @@ __device__ __forceinline__ void merge_product_fma(Smem<NMAX, G>& S, const Plan& 
         // rows past rend and columns past qend read padding or neighbouring entries; their
         // sums are never stored
         const float* qrow = S.Q + r0 * LD;
+#pragma unroll 2
         for (int c = c0; c < c1; ++c) {
             const float* mrow = S.M + S.rank[c] * LD + q0;
             float mv[PC];
@@ -823,10 +834,11 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 "l"(Ab), "r"(bytes), "r"(bar)
                 : "memory");
         }
-        if (!mbar_wait_bounded(bar, phase, 2000000000ull)) {
+        if (!mbar_wait_bounded(bar, phase, kp.stage_wait_ns)) {
             timed_out = true;
-            // wait once more, again bounded, for the copy still in flight
-            mbar_wait_bounded(bar, phase, 2000000000ull);
+            // wait once more, again bounded, for the copy still in flight: once it has landed the
+            // mbarrier phase is known again and the team can go on with its next matrix
+            if (!mbar_wait_bounded(bar, phase, kDrainWaitNs)) atomicOr(&S.info, kInfoUndrained);
         }
         phase ^= 1u;
     } else {
@@ -864,10 +876,10 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         const float qnan = __int_as_float(0x7fc00000);
         for (int i = tid; i < n; i += NT) Wb[i] = qnan;
         for (int i = tid; i < n * n; i += NT) Vb[i] = qnan;
-        if (info_b && tid == 0) *info_b = S.info;
-        const bool stop = (S.info & BED_INFO_TIMEOUT) != 0;
+        if (info_b && tid == 0) *info_b = S.info & ~kInfoUndrained;
+        const bool stop = (S.info & kInfoUndrained) != 0;
         team_sync<NT>(bar_id);
-        return !stop;  // after a timeout the barrier phase is no longer known: the caller stops
+        return !stop;  // a copy still in flight: the mbarrier phase is no longer known, the caller stops
     }
     amax = S.red[0];
 #pragma unroll
@@ -1145,6 +1157,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 const float* z2 = &S.Q[mid * LD];        // first row of Q2
                 zc = (c < mid) ? sig * z1[c] : z2[c];
                 kc = sort_key(S.lam[c]);
+#pragma unroll 4
                 for (int c2 = lo + sub; c2 < hi; c2 += G) {
                     const float l2 = S.lam[c2];
                     const float k2 = sort_key(l2);
@@ -1186,6 +1199,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             const int t = pos;
             int nb = 0, K = 0;
             if (act)
+#pragma unroll 4
                 for (int p2 = lo + sub; p2 < hi; p2 += G) {
                     const int nd = !S.defl[p2];
                     K += nd;
@@ -1306,6 +1320,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 // two ratios per division: their indices differ by G >= 2, so at most one of the two
                 // numerators is a root hugging d_i, and both products stay far inside the FP32 range
                 int j = sub;
+#pragma unroll 2
                 for (; j + G < K - 1; j += 2 * G) {
                     const int jb = j + G;
                     const float na = (S.cdz[S.org[lo + j]].x - di) + S.tq[lo + j];  // lambda_j - d_i
@@ -1336,6 +1351,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 if (q < K) {
                     const float dorg = S.cdz[S.org[lo + q]].x;
                     const float tq = S.tq[lo + q];
+#pragma unroll 4
                     for (int i = sub; i < K; i += G) {
                         const float v = __fdividef(S.zh[lo + i], (S.cdz[lo + i].x - dorg) - tq);
                         S.M[S.inv[lo + i] * LD + cq] = v;
@@ -1531,6 +1547,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         int r = 0;
         if (pos < n) {
             const float kc = sort_key(S.lam[pos]);
+#pragma unroll 4
             for (int t2 = sub; t2 < n; t2 += G) {
                 const float k2 = sort_key(S.lam[t2]);
                 r += (k2 < kc) || (k2 == kc && t2 < pos);
@@ -1546,6 +1563,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         int im = 0;
         if (pos < n) {
             src = S.outc[pos];
+#pragma unroll 4
             for (int i = sub; i < n; i += G) {
                 const float v = fabsf(S.Q[i * LD + src]);
                 if (v > vm) {

@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(1024) ragged_order_kernel(const int32_t* __res
 }
 
 struct RaggedArgs {
+    const MatDesc* desc;  // descriptor form (the request loop): per-matrix addresses, plain loads
     const float* A;
     const int64_t* offsets;
     const int32_t* ns;
@@ -162,12 +163,27 @@ __device__ __forceinline__ bool run_team(unsigned char* smem, const RaggedArgs& 
     const int n = a.ns[i];
     const Plan& plan = g_plans[tune.leaf[n] - 1][n];
     Smem<NMAX, G>& S = *reinterpret_cast<Smem<NMAX, G>*>(smem + team * slice_bytes<NMAX, G>());
-    const float* Ab = a.A + a.offsets[i];
-    const bool bulk = (n % 2 == 0) && ((reinterpret_cast<uintptr_t>(Ab) & 15u) == 0);
+    const float* Ab;
+    float *Wb, *Vb;
+    int32_t* Ib;
+    bool bulk;
+    if (a.desc) {
+        const MatDesc d = a.desc[i];
+        Ab = d.A;
+        Wb = d.W;
+        Vb = d.V;
+        Ib = d.info;
+        bulk = false;  // the input may be page-locked host memory
+    } else {
+        Ab = a.A + a.offsets[i];
+        Wb = a.W + a.w_offsets[i];
+        Vb = a.V + a.offsets[i];
+        Ib = a.info ? a.info + i : nullptr;
+        bulk = (n % 2 == 0) && ((reinterpret_cast<uintptr_t>(Ab) & 15u) == 0);
+    }
     uint32_t phase = phases[team];
-    const bool ok = solve_matrix<NMAX, G>(S, plan, kp, ttid, 1 + team, smem_u32(&mbars[team]), phase, Ab,
-                                          a.W + a.w_offsets[i], a.V + a.offsets[i],
-                                          a.info ? a.info + i : nullptr, a.counters, bulk);
+    const bool ok = solve_matrix<NMAX, G>(S, plan, kp, ttid, 1 + team, smem_u32(&mbars[team]), phase, Ab, Wb, Vb,
+                                          Ib, a.counters, bulk);
     if (ttid == 0) phases[team] = phase;
     return ok;
 }
@@ -207,7 +223,7 @@ __global__ void __launch_bounds__(kRaggedThreads, 4)
             if (tid < 192) ok = run_team<48, 4>(smem_raw, a, tune, kp, 0, tid, first, last, mbars, phases);
             break;
         }
-        if (!ok) s_stop = 1;  // a staging copy timed out: this block stops taking work
+        if (!ok) s_stop = 1;  // a timed-out staging copy never landed: this block stops taking work
         // the next unit may stage a matrix by bulk copy into memory any thread wrote in this one
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -270,7 +286,29 @@ cudaError_t launch_ragged(const float* A, const int64_t* offsets, const int32_t*
     ragged_order_kernel<<<1, 1024, 0, stream>>>(ns, count, tune, hdr, order, info);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    RaggedArgs a{A, offsets, ns, W, w_offsets, V, info, hdr, order, counters};
+    RaggedArgs a{nullptr, A, offsets, ns, W, w_offsets, V, info, hdr, order, counters};
+    ragged_kernel<<<grid, kRaggedThreads, kRaggedSmem, stream>>>(a, tune, kp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ragged_desc(const MatDesc* desc, const int32_t* ns, int64_t count,
+                               const bed_ragged_tuning& tuning, const KParams& kp, void* workspace,
+                               cudaStream_t stream)
+{
+    int grid = 0;
+    cudaError_t e = ragged_setup(&grid);
+    if (e != cudaSuccess) return e;
+    RaggedTune tune;
+    std::memcpy(tune.team, tuning.team, sizeof tune.team);
+    std::memcpy(tune.leaf, tuning.leaf, sizeof tune.leaf);
+    RaggedHeader* hdr = static_cast<RaggedHeader*>(workspace);
+    int32_t* order = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) + sizeof(RaggedHeader));
+    // sizes outside [1, 64] are flagged through the descriptors' info words by the persistent kernel's
+    // callers (the request loop admits only valid sizes), so the ordering pass gets no info array
+    ragged_order_kernel<<<1, 1024, 0, stream>>>(ns, count, tune, hdr, order, nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    RaggedArgs a{desc, nullptr, nullptr, ns, nullptr, nullptr, nullptr, nullptr, hdr, order, nullptr};
     ragged_kernel<<<grid, kRaggedThreads, kRaggedSmem, stream>>>(a, tune, kp);
     return cudaGetLastError();
 }

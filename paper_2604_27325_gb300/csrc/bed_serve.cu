@@ -1,12 +1,15 @@
 // Native request loop: continuous batching of eigendecomposition requests on one GPU.
 //
 // Host code only (C++ threads and the CUDA runtime); the device work is the library's launches.
-// Requests are admitted in arrival order while their device memory (inputs, eigenvectors,
-// eigenvalues) fits the device arena and their results fit the pinned host result arena. Everything
-// admitted since the previous launch goes into one ragged launch on a free stream slot (several
-// launches overlap on the device); the completion thread waits for the oldest launch's event, frees
-// the device space of the requests it carried and marks them done. In FIFO mode each request is one
-// uniform-size launch on a single stream instead (the plain per-request baseline).
+// Requests are admitted in arrival order while their memory fits: the pinned host result arena always,
+// the device arena for what is staged there (inputs that are not page-locked, or everything when
+// zero-copy is off). Everything admitted since the previous launch goes into one launch on a free
+// stream slot (several launches overlap on the device). With zero-copy (the default) a launch reads
+// page-locked inputs in place and writes eigenvalues, eigenvectors and flags straight into the
+// result arena, so a request's latency holds no copy; its per-matrix addresses are handed to the
+// kernels as descriptors in page-locked memory. The completion thread polls every in-flight launch
+// and retires each as soon as it is done, whatever the order. In FIFO mode each request is one
+// uniform-size launch on a single stream instead (the plain per-request baseline, same data path).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -68,6 +71,7 @@ public:
     }
     int64_t capacity() const { return cap_; }
     int64_t used() const { return used_; }
+    // 4-element (16-byte) granules keep every block 16-byte aligned
     static int64_t pad(int64_t x) { return (std::max<int64_t>(x, 1) + 3) / 4 * 4; }
 
 private:
@@ -77,11 +81,15 @@ private:
 
 struct Request {
     int64_t id;
-    const float* A;
+    const float* A;  // caller's host buffer
     int b, n;
     double t_submit = 0, t_done = 0;
-    int64_t a_off = -1, w_off = -1, h_off = -1;
-    int state = 0;  // 0 pending, 1 in flight, 2 done
+    const float* A_in = nullptr;  // device-visible address of A when it is read in place (zero-copy)
+    bool checked = false;         // A_in decided (at admission)
+    int64_t a_off = -1;           // device input arena (staged input); the eigenvector arena uses it too
+    int64_t w_off = -1;           // device eigenvalue arena (staged outputs)
+    int64_t h_off = -1;           // pinned result arena: [V | W | info]
+    int state = 0;                // 0 pending, 1 in flight, 2 done
     int32_t status = BED_OK;
     int64_t dev_elems() const { return int64_t(b) * n * n; }
     int64_t w_elems() const { return int64_t(b) * n; }
@@ -91,13 +99,11 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t event = nullptr;
-    int64_t* off_h = nullptr;
-    int32_t* ns_h = nullptr;
-    int64_t* woff_h = nullptr;
-    int64_t* off_d = nullptr;
-    int32_t* ns_d = nullptr;
-    int64_t* woff_d = nullptr;
-    int32_t* info_d = nullptr;
+    bed::MatDesc* desc_h = nullptr;  // page-locked descriptors of the launch's matrices
+    int32_t* ns_h = nullptr;         // page-locked sizes
+    const bed::MatDesc* desc_d = nullptr;  // their device-visible addresses
+    const int32_t* ns_d = nullptr;
+    int32_t* info_d = nullptr;       // flags of staged outputs
     void* ws = nullptr;
     size_t ws_bytes = 0;
     bool busy = false;
@@ -115,8 +121,9 @@ struct bed_server {
     bed_params params{};
     bed_ragged_tuning tuning{};
     int device = 0;
-    float* dev = nullptr;       // [A arena | V arena | W arena]
-    float* host = nullptr;      // pinned results: per request [V | W | info]
+    float* dev = nullptr;   // [A arena | V arena | W arena]
+    float* host = nullptr;  // pinned results: per request [V | W | info]
+    float* host_d = nullptr;  // device-visible address of `host`
     int64_t cap_av = 0, cap_w = 0;
     Arena* av = nullptr;
     Arena* w = nullptr;
@@ -128,6 +135,7 @@ struct bed_server {
     std::mutex mu;
     std::condition_variable cv;
     bool running = true;
+    int launching = 0;  // batches taken from `pending` whose launch is not yet in `inflight`
     int64_t next_id = 1;
     // statistics
     std::vector<double> lat;
@@ -147,72 +155,96 @@ void fail_request(bed_server* s, Request* r, int32_t status)
     (void)s;
 }
 
+// Releases the device arena space a request holds (host result space stays until bed_server_release).
+void release_device(bed_server* s, Request* r)
+{
+    if (r->a_off >= 0) s->av->release(r->a_off, r->dev_elems());
+    if (r->w_off >= 0) s->w->release(r->w_off, r->w_elems());
+    r->a_off = r->w_off = -1;
+}
+
 void launch(bed_server* s, int si, std::vector<Request*>& batch)
 {
     Slot& sl = s->slots[si];
-    float* A = s->dev;
-    float* V = s->dev + s->cap_av;
-    float* W = s->dev + 2 * s->cap_av;
+    float* Ad = s->dev;
+    float* Vd = s->dev + s->cap_av;
+    float* Wd = s->dev + 2 * s->cap_av;
+    const bool zc = s->cfg.zero_copy != 0;
+    cudaError_t e = cudaSuccess;
+    bed_status st = BED_OK;
+    // inputs that are not read in place are copied into the device arena first
+    for (Request* r : batch)
+        if (e == cudaSuccess && !r->A_in)
+            e = cudaMemcpyAsync(Ad + r->a_off, r->A, r->dev_elems() * sizeof(float), cudaMemcpyHostToDevice,
+                                sl.stream);
+    // addresses of every matrix: input in place or staged; outputs in the result arena (zero-copy) or
+    // in the device arenas
     int64_t k = 0;
     for (Request* r : batch) {
+        const float* a = r->A_in ? r->A_in : Ad + r->a_off;
+        float* hv = s->host_d + r->h_off;
+        float* hw = hv + r->dev_elems();
+        int32_t* hi = reinterpret_cast<int32_t*>(hw + r->w_elems());
         for (int j = 0; j < r->b; ++j) {
-            sl.off_h[k + j] = r->a_off + int64_t(j) * r->n * r->n;
-            sl.woff_h[k + j] = r->w_off + int64_t(j) * r->n;
+            bed::MatDesc& d = sl.desc_h[k + j];
+            d.A = a + int64_t(j) * r->n * r->n;
+            d.V = zc ? hv + int64_t(j) * r->n * r->n : Vd + r->a_off + int64_t(j) * r->n * r->n;
+            d.W = zc ? hw + int64_t(j) * r->n : Wd + r->w_off + int64_t(j) * r->n;
+            d.info = zc ? hi + j : sl.info_d + k + j;
             sl.ns_h[k + j] = r->n;
         }
         k += r->b;
     }
-    cudaError_t e = cudaSuccess;
-    bed_status st = BED_OK;
-    // a launch carrying one request runs the uniform-size kernel directly (no ordering pass)
-    const bool ragged = s->cfg.mode == 0 && batch.size() > 1;
-    if (ragged) {
-        e = cudaMemcpyAsync(sl.off_d, sl.off_h, k * sizeof(int64_t), cudaMemcpyHostToDevice, sl.stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(sl.ns_d, sl.ns_h, k * sizeof(int32_t), cudaMemcpyHostToDevice, sl.stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sl.woff_d, sl.woff_h, k * sizeof(int64_t), cudaMemcpyHostToDevice, sl.stream);
-    }
-    for (Request* r : batch)
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(A + r->a_off, r->A, r->dev_elems() * sizeof(float), cudaMemcpyHostToDevice, sl.stream);
     if (e == cudaSuccess) {
-        if (ragged) {
-            st = bed_eigh_ragged_f32(A, sl.off_d, sl.ns_d, k, W, sl.woff_d, V, sl.info_d, &s->params, &s->tuning,
-                                     sl.ws, sl.ws_bytes, nullptr, sl.stream);
+        if (s->cfg.mode == 0 && batch.size() > 1) {
+            bed_params prm;
+            bed::KParams kp;
+            if (!bed::make_kparams(&s->params, &prm, &kp)) {
+                st = BED_ERR_INVALID_ARG;
+            } else {
+                e = bed::launch_ragged_desc(sl.desc_d, sl.ns_d, k, s->tuning, kp, sl.ws, sl.stream);
+            }
         } else {
+            // one request: the uniform kernel on its contiguous matrices. In batching mode it takes the
+            // team shape and leaf size the ragged kernel gives this n, so that a request's results do not
+            // depend on whether it shared a launch (team types 0..4 have 256, 128, 64, 32 and 192 threads)
             Request* r = batch[0];
+            const bed::MatDesc& d = sl.desc_h[0];
             bed_params p = s->params;
             if (s->cfg.mode == 0) {
-                // the team shape and leaf size the ragged kernel gives this n, so that a request's results
-                // do not depend on whether it was batched with others (team types 0..4 have 256, 128, 64,
-                // 32 and 192 threads)
                 const int tt = s->tuning.team[r->n];
                 p.threads_per_matrix = (tt == 4) ? 192 : (256 >> tt);
                 p.leaf_size = s->tuning.leaf[r->n];
             }
-            st = bed_eigh_f32(A + r->a_off, W + r->w_off, V + r->a_off, sl.info_d, r->b, r->n, &p, sl.stream);
+            st = bed::eigh_common(d.A, d.W, d.V, d.info, r->b, r->n, &p, nullptr, sl.stream, true);
         }
     }
-    k = 0;
-    for (Request* r : batch) {
-        float* hv = s->host + r->h_off;
-        float* hw = hv + r->dev_elems();
-        int32_t* hi = reinterpret_cast<int32_t*>(hw + r->w_elems());
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(hv, V + r->a_off, r->dev_elems() * sizeof(float), cudaMemcpyDeviceToHost, sl.stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(hw, W + r->w_off, r->w_elems() * sizeof(float), cudaMemcpyDeviceToHost, sl.stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(hi, sl.info_d + k, r->b * sizeof(int32_t), cudaMemcpyDeviceToHost, sl.stream);
-        k += r->b;
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(sl.event, sl.stream);
-    std::lock_guard<std::mutex> lock(s->mu);
-    if (e != cudaSuccess || st != BED_OK) {
-        for (Request* r : batch) fail_request(s, r, st != BED_OK ? st : BED_ERR_CUDA);
+    if (!zc) {
+        k = 0;
         for (Request* r : batch) {
-            s->av->release(r->a_off, r->dev_elems());
-            s->w->release(r->w_off, r->w_elems());
+            float* hv = s->host + r->h_off;
+            float* hw = hv + r->dev_elems();
+            int32_t* hi = reinterpret_cast<int32_t*>(hw + r->w_elems());
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hv, Vd + r->a_off, r->dev_elems() * sizeof(float), cudaMemcpyDeviceToHost,
+                                    sl.stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hw, Wd + r->w_off, r->w_elems() * sizeof(float), cudaMemcpyDeviceToHost,
+                                    sl.stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hi, sl.info_d + k, r->b * sizeof(int32_t), cudaMemcpyDeviceToHost, sl.stream);
+            k += r->b;
+        }
+    }
+    if (e == cudaSuccess && st == BED_OK) e = cudaEventRecord(sl.event, sl.stream);
+    std::lock_guard<std::mutex> lock(s->mu);
+    --s->launching;
+    if (e != cudaSuccess || st != BED_OK) {
+        // what was enqueued before the failure may still run: wait for it before the space is reused
+        cudaStreamSynchronize(sl.stream);
+        for (Request* r : batch) {
+            fail_request(s, r, st != BED_OK ? st : BED_ERR_CUDA);
+            release_device(s, r);
         }
         sl.busy = false;
         s->cv.notify_all();
@@ -226,6 +258,7 @@ void launch(bed_server* s, int si, std::vector<Request*>& batch)
 void scheduler(bed_server* s)
 {
     cudaSetDevice(s->device);
+    const bool zc = s->cfg.zero_copy != 0;
     std::unique_lock<std::mutex> lock(s->mu);
     for (;;) {
         s->cv.wait(lock, [&] {
@@ -240,25 +273,39 @@ void scheduler(bed_server* s)
                 si = int(i);
                 break;
             }
-        if (si < 0) continue;
+        if (si < 0) {  // shutting down with every slot busy: wait for the completion thread
+            s->cv.wait_for(lock, std::chrono::microseconds(200));
+            continue;
+        }
         // admit from the head, in order, while everything fits
         std::vector<Request*> batch;
         int64_t count = 0;
-        const int64_t cap = s->cfg.mode == 0 ? s->cfg.max_launch_matrices : 0;
+        const int64_t cap = s->cfg.max_launch_matrices;
         while (!s->pending.empty()) {
             Request* r = s->pending.front();
             if (!batch.empty() && (s->cfg.mode != 0 || count + r->b > cap)) break;
-            const int64_t a = s->av->alloc(r->dev_elems());
-            if (a < 0) break;
-            const int64_t wo = s->w->alloc(r->w_elems());
-            if (wo < 0) {
-                s->av->release(a, r->dev_elems());
-                break;
+            if (!r->checked) {  // in place only if the whole input is page-locked and mapped
+                r->A_in = zc ? static_cast<const float*>(bed::mapped_range(r->A, r->dev_elems() * sizeof(float)))
+                             : nullptr;
+                r->checked = true;
+            }
+            const bool stage_in = !r->A_in, stage_out = !zc;
+            int64_t a = -1, wo = -1;
+            if (stage_in || stage_out) {
+                a = s->av->alloc(r->dev_elems());
+                if (a < 0) break;
+            }
+            if (stage_out) {
+                wo = s->w->alloc(r->w_elems());
+                if (wo < 0) {
+                    s->av->release(a, r->dev_elems());
+                    break;
+                }
             }
             const int64_t ho = s->h->alloc(r->host_elems());
             if (ho < 0) {
-                s->av->release(a, r->dev_elems());
-                s->w->release(wo, r->w_elems());
+                if (a >= 0) s->av->release(a, r->dev_elems());
+                if (wo >= 0) s->w->release(wo, r->w_elems());
                 break;
             }
             r->a_off = a;
@@ -269,48 +316,71 @@ void scheduler(bed_server* s)
             batch.push_back(r);
             count += r->b;
         }
-        if (batch.empty()) {  // the head waits for memory that the completion thread will free
+        if (batch.empty()) {  // the head waits for memory that completions or releases will free
+            if (!s->running && s->inflight.empty() && s->launching == 0) {
+                // shutting down and nothing in flight can free memory any more: drop what cannot fit
+                for (Request* r : s->pending) fail_request(s, r, BED_ERR_TOO_LARGE);
+                s->pending.clear();
+                s->cv.notify_all();
+                continue;
+            }
             s->cv.wait_for(lock, std::chrono::microseconds(200));
             continue;
         }
         s->peak_dev = std::max(s->peak_dev, s->dev_bytes_in_use());
         s->slots[si].busy = true;
+        ++s->launching;
         lock.unlock();
         launch(s, si, batch);
         lock.lock();
     }
 }
 
+// Polls every in-flight launch (a copy of their events is taken under the lock, queried outside it) and
+// retires each completed one at once, so that a short launch is not held behind a longer, older one.
 void completer(bed_server* s)
 {
     cudaSetDevice(s->device);
+    std::vector<std::pair<int, cudaEvent_t>> evs;
+    std::vector<std::pair<int, cudaError_t>> fin;
     std::unique_lock<std::mutex> lock(s->mu);
     for (;;) {
-        s->cv.wait(lock, [&] { return !s->inflight.empty() || (!s->running && s->pending.empty()); });
+        s->cv.wait(lock, [&] {
+            return !s->inflight.empty() || (!s->running && s->pending.empty() && s->launching == 0);
+        });
         if (s->inflight.empty()) {
-            if (!s->running && s->pending.empty()) return;
+            if (!s->running && s->pending.empty() && s->launching == 0) return;
             continue;
         }
-        Launch L = s->inflight.front();
-        s->inflight.pop_front();
-        cudaEvent_t ev = s->slots[L.slot].event;
+        evs.clear();
+        for (const Launch& L : s->inflight) evs.emplace_back(L.slot, s->slots[L.slot].event);
         lock.unlock();
-        const cudaError_t e = cudaEventSynchronize(ev);
-        const double t = now_s();
-        lock.lock();
-        for (Request* r : L.reqs) {
-            s->av->release(r->a_off, r->dev_elems());
-            s->w->release(r->w_off, r->w_elems());
-            r->state = 2;
-            r->t_done = t;
-            r->status = e == cudaSuccess ? BED_OK : BED_ERR_CUDA;
-            s->lat.push_back(t - r->t_submit);
-            ++s->n_requests;
-            s->n_matrices += r->b;
-            s->t_last = t;
+        fin.clear();
+        for (const auto& x : evs) {
+            const cudaError_t q = cudaEventQuery(x.second);
+            if (q != cudaErrorNotReady) fin.emplace_back(x.first, q);
         }
-        s->slots[L.slot].busy = false;
-        s->cv.notify_all();
+        const double t = now_s();
+        if (fin.empty()) std::this_thread::yield();  // launches in flight: keep polling
+        lock.lock();
+        for (const auto& f : fin) {
+            auto it = std::find_if(s->inflight.begin(), s->inflight.end(),
+                                   [&](const Launch& L) { return L.slot == f.first; });
+            if (it == s->inflight.end()) continue;
+            for (Request* r : it->reqs) {
+                release_device(s, r);
+                r->state = 2;
+                r->t_done = t;
+                r->status = f.second == cudaSuccess ? BED_OK : BED_ERR_CUDA;
+                s->lat.push_back(t - r->t_submit);
+                ++s->n_requests;
+                s->n_matrices += r->b;
+                s->t_last = t;
+            }
+            s->slots[it->slot].busy = false;
+            s->inflight.erase(it);
+        }
+        if (!fin.empty()) s->cv.notify_all();
     }
 }
 
@@ -326,6 +396,7 @@ void bed_server_default_config(bed_server_config* c)
     c->streams = 3;
     c->max_launch_matrices = 16384;
     c->mode = 0;
+    c->zero_copy = 1;
 }
 
 bed_status bed_server_create(const bed_server_config* cfg, const bed_params* p, const bed_ragged_tuning* t,
@@ -337,8 +408,14 @@ bed_status bed_server_create(const bed_server_config* cfg, const bed_params* p, 
     bed_server_default_config(&c);
     if (cfg) c = *cfg;
     if (c.streams < 1 || c.streams > 16 || c.max_launch_matrices < 1 || c.max_launch_matrices > (1 << 24) ||
-        (c.mode != 0 && c.mode != 1) || c.device_budget_bytes < 4096 || c.host_result_bytes < 4096)
+        (c.mode != 0 && c.mode != 1) || (c.zero_copy != 0 && c.zero_copy != 1) || c.device_budget_bytes < 4096 ||
+        c.host_result_bytes < 4096)
         return BED_ERR_INVALID_ARG;
+    {
+        bed_params prm;
+        bed::KParams kp;
+        if (!bed::make_kparams(p, &prm, &kp)) return BED_ERR_INVALID_ARG;
+    }
     if (c.mode == 1) c.streams = 1;
     auto* s = new bed_server();
     s->cfg = c;
@@ -352,7 +429,8 @@ bed_status bed_server_create(const bed_server_config* cfg, const bed_params* p, 
     s->cap_av = units * 15 / 32 / 4 * 4;
     s->cap_w = (units - 2 * s->cap_av) / 4 * 4;
     cudaError_t e = cudaMalloc(&s->dev, size_t(2 * s->cap_av + s->cap_w) * sizeof(float));
-    if (e == cudaSuccess) e = cudaHostAlloc(&s->host, c.host_result_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->host, c.host_result_bytes, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->host_d), s->host, 0);
     s->av = new Arena(s->cap_av);
     s->w = new Arena(s->cap_w);
     s->h = new Arena(int64_t(c.host_result_bytes / 4));
@@ -361,12 +439,12 @@ bed_status bed_server_create(const bed_server_config* cfg, const bed_params* p, 
     for (auto& sl : s->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.event, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaHostAlloc(&sl.off_h, m * sizeof(int64_t), cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaHostAlloc(&sl.woff_h, m * sizeof(int64_t), cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaHostAlloc(&sl.ns_h, m * sizeof(int32_t), cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaMalloc(&sl.off_d, m * sizeof(int64_t));
-        if (e == cudaSuccess) e = cudaMalloc(&sl.woff_d, m * sizeof(int64_t));
-        if (e == cudaSuccess) e = cudaMalloc(&sl.ns_d, m * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaHostAlloc(&sl.desc_h, m * sizeof(bed::MatDesc), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostAlloc(&sl.ns_h, m * sizeof(int32_t), cudaHostAllocMapped);
+        if (e == cudaSuccess)
+            e = cudaHostGetDevicePointer(reinterpret_cast<void**>(const_cast<bed::MatDesc**>(&sl.desc_d)), sl.desc_h, 0);
+        if (e == cudaSuccess)
+            e = cudaHostGetDevicePointer(reinterpret_cast<void**>(const_cast<int32_t**>(&sl.ns_d)), sl.ns_h, 0);
         if (e == cudaSuccess) e = cudaMalloc(&sl.info_d, m * sizeof(int32_t));
         sl.ws_bytes = bed_eigh_ragged_workspace_size(m);
         if (e == cudaSuccess) e = cudaMalloc(&sl.ws, sl.ws_bytes);
@@ -374,7 +452,7 @@ bed_status bed_server_create(const bed_server_config* cfg, const bed_params* p, 
     if (e != cudaSuccess) {
         s->running = false;
         bed_server_destroy(s);
-        return BED_ERR_CUDA;
+        return bed::cuda_fail(e);
     }
     s->sched = std::thread(scheduler, s);
     s->done = std::thread(completer, s);
@@ -394,9 +472,9 @@ bed_status bed_server_submit(bed_server* s, const float* A_host, int32_t b, int3
     r->id = s->next_id++;
     s->reqs[r->id] = r;
     *request_id = r->id;
+    // every launch's descriptor arrays hold max_launch_matrices entries, in both modes
     if (Arena::pad(r->dev_elems()) > s->av->capacity() || Arena::pad(r->w_elems()) > s->w->capacity() ||
-        Arena::pad(r->host_elems()) > s->h->capacity() ||
-        (s->cfg.mode == 0 && r->b > s->cfg.max_launch_matrices)) {
+        Arena::pad(r->host_elems()) > s->h->capacity() || r->b > s->cfg.max_launch_matrices) {
         fail_request(s, r, BED_ERR_TOO_LARGE);
         return BED_ERR_TOO_LARGE;
     }
@@ -488,17 +566,12 @@ void bed_server_destroy(bed_server* s)
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.event) cudaEventDestroy(sl.event);
         if (sl.stream) cudaStreamDestroy(sl.stream);
-        cudaFreeHost(sl.off_h);
-        cudaFreeHost(sl.woff_h);
+        cudaFreeHost(sl.desc_h);
         cudaFreeHost(sl.ns_h);
-        cudaFree(sl.off_d);
-        cudaFree(sl.woff_d);
-        cudaFree(sl.ns_d);
         cudaFree(sl.info_d);
         cudaFree(sl.ws);
     }
     for (auto& kv : s->reqs) delete kv.second;
-    for (Request* r : s->pending) (void)r;
     cudaFree(s->dev);
     cudaFreeHost(s->host);
     delete s->av;

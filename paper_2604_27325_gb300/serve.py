@@ -436,19 +436,23 @@ class NativeServer:
 
     def __init__(self, budget_bytes: int = 4 << 30, host_result_bytes: int = 2 << 30, streams: int = 3,
                  max_launch_matrices: int = 16384, mode: str = "batch", tuning: B.bed_ragged_tuning | None = None,
-                 params: B.bed_params | None = None):
+                 params: B.bed_params | None = None, zero_copy: bool = True):
         cfg = B.bed_server_default_config()
         cfg.device_budget_bytes, cfg.host_result_bytes = int(budget_bytes), int(host_result_bytes)
         cfg.streams, cfg.max_launch_matrices = int(streams), int(max_launch_matrices)
         cfg.mode = 0 if mode == "batch" else 1
+        cfg.zero_copy = 1 if zero_copy else 0
         st, self.h = B.bed_server_create(cfg, params, tuning)
         B._check(st)
         self.keep = {}  # request id -> input tensor, alive until the request completes
 
-    def submit(self, A: torch.Tensor) -> int:
-        """Queue a pinned float32 [b, n, n] CPU tensor; returns the request id (BedError if refused)."""
-        if not A.is_pinned():
-            A = A.contiguous().pin_memory()
+    def submit(self, A: torch.Tensor, pin: bool = True) -> int:
+        """Queue a float32 [b, n, n] CPU tensor (copied to page-locked memory first unless ``pin`` is
+        False, in which case the server stages it through its device arena); returns the request id
+        (BedError if refused)."""
+        A = A.contiguous()
+        if pin and not A.is_pinned():
+            A = A.pin_memory()
         st, rid = B.bed_server_submit(self.h, A.data_ptr(), int(A.shape[0]), int(A.shape[-1]))
         self.keep[rid] = A
         if st != B.BED_OK:
@@ -495,46 +499,66 @@ class NativeServer:
 
 def run_load_native(server: NativeServer, rate: float = 2000.0, seconds: float = 60.0, seed: int = 5001,
                     pool=None, nmin: int = 8, nmax: int = 64, bmax: int = 256, warmup_s: float = 1.0):
-    """Poisson load (as ``run_load``) on a NativeServer; a consumer thread waits for and releases results
-    in submission order while requests keep arriving. Returns the server's statistics of the measured run."""
-    import queue
+    """Poisson load on a NativeServer: arrivals at `rate` requests/s for `seconds`, each request
+    b ~ U{1..bmax} matrices of one size n ~ U{nmin..nmax} drawn from the pinned pool (the pool's memory
+    is submitted in place, by address). One thread submits on schedule and, between arrivals, releases
+    completed requests in submission order (a zero-timeout wait on the oldest), so no second Python
+    thread competes for the interpreter. A warm-up of `warmup_s` at the same rate runs first and is not
+    counted. Returns the server's statistics of the measured run plus the offered and achieved rates."""
+    import collections
 
     pool = pool or request_pool(seed, nmin, nmax, bmax)
     if warmup_s > 0:
         run_load_native(server, rate, warmup_s, seed + 1, pool, nmin, nmax, bmax, warmup_s=0.0)
         server.reset_stats()
-    ids = queue.Queue()
-
-    def consume():
-        while True:
-            rid = ids.get()
-            if rid is None:
-                return
-            st, _, _, _ = B.bed_server_wait(server.h, rid, -1.0)
-            server.keep.pop(rid, None)
-            B.bed_server_release(server.h, rid)
-
-    th = threading.Thread(target=consume, daemon=True)
-    th.start()
     rng = np.random.default_rng(seed)
+    count = max(1, int(rate * seconds * 1.2) + 16)
+    t_arr = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    t_arr = t_arr[t_arr <= seconds]
+    ns = rng.integers(nmin, nmax + 1, size=len(t_arr))
+    bs = rng.integers(1, bmax + 1, size=len(t_arr))
+    u = rng.random(len(t_arr))
+    base = {n: (pool[n].data_ptr(), pool[n].shape[0]) for n in range(nmin, nmax + 1)}
+    h = server.h
+    lib = B.lib()
+    wait_c, rel_c = lib.bed_server_wait, lib.bed_server_release
+    outstanding = collections.deque()
+
+    def drain(block: bool):
+        while outstanding:
+            rid = outstanding[0]
+            st = wait_c(h, rid, -1.0 if block else 0.0, None, None, None)
+            if st == B.BED_ERR_TIMEOUT:
+                return
+            rel_c(h, rid)
+            outstanding.popleft()
+
+    rid = C.c_int64()
+    submit_c = lib.bed_server_submit
     t0 = time.perf_counter()
-    t = 0.0
-    offered = 0
-    while True:
-        t += rng.exponential(1.0 / rate)
-        if t > seconds:
-            break
-        n = int(rng.integers(nmin, nmax + 1))
-        b = int(rng.integers(1, bmax + 1))
-        start = int(rng.integers(0, pool[n].shape[0] - b + 1))
-        delay = t0 + t - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        ids.put(server.submit(pool[n][start: start + b]))
-        offered += 1
-    ids.put(None)
-    th.join()
+    for k in range(len(t_arr)):
+        n, b = int(ns[k]), int(bs[k])
+        ptr, rows = base[n]
+        start = int(u[k] * (rows - b + 1))
+        last = -1.0
+        while True:
+            now = time.perf_counter() - t0
+            if now >= t_arr[k]:
+                break
+            if outstanding and now - last > 20e-6:  # poll completions at most every 20 us
+                drain(False)
+                last = now
+        st = submit_c(h, C.c_void_p(ptr + 4 * start * n * n), b, n, C.byref(rid))
+        if st != B.BED_OK:
+            raise B.BedError(B.bed_status_string(st))
+        outstanding.append(rid.value)
+    t_sub = time.perf_counter() - t0
+    drain(True)
     out = server.stats()
-    out["offered_requests"] = offered
+    out["offered_requests"] = len(t_arr)
+    out["offered_rate"] = rate
+    out["achieved_submit_rate"] = len(t_arr) / max(t_sub, 1e-9)
     out["wall_s"] = time.perf_counter() - t0
+    if out.get("launches"):
+        out["requests_per_launch"] = out["requests"] / out["launches"]
     return out

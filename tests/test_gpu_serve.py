@@ -99,7 +99,8 @@ def test_native_server_same_results_alone_and_in_the_mix():
 def test_native_server_budget_and_fifo_mode():
     reqs = _requests(22, 30)
     budget = 3 << 20
-    srv = serve.NativeServer(budget_bytes=budget, host_result_bytes=64 << 20, streams=2)
+    # inputs and results through the device arena: admission is held to the device budget
+    srv = serve.NativeServer(budget_bytes=budget, host_result_bytes=64 << 20, streams=2, zero_copy=False)
     with pytest.raises(B.BedError):
         srv.submit(torch.zeros(256, 64, 64).pin_memory())
     ids = [srv.submit(r) for r in reqs]
@@ -124,3 +125,49 @@ def test_native_short_poisson_run():
     out = serve.run_load_native(srv, rate=1000.0, seconds=1.0, seed=23)
     srv.close()
     assert out["requests"] == out["offered_requests"] and out["p99_ms"] > 0
+
+
+def test_native_server_zero_copy_equals_staged_and_unpinned_inputs_are_staged():
+    """Zero-copy (inputs read in place, results written in place) and the staged data path run the same
+    kernels on the same matrices: bitwise equal results. An input that is not page-locked is staged
+    through the device arena even in zero-copy mode, with the same results."""
+    reqs = _requests(31, 24)
+    out = {}
+    for zc in (True, False):
+        srv = serve.NativeServer(budget_bytes=256 << 20, host_result_bytes=256 << 20, zero_copy=zc)
+        ids = [srv.submit(r) for r in reqs]
+        out[zc] = [srv.result(i, r.shape[0], r.shape[-1]) for i, r in zip(ids, reqs)]
+        if zc:
+            assert srv.stats()["peak_device_bytes"] == 0  # nothing staged
+            ids = [srv.submit(r.clone(), pin=False) for r in reqs[:6]]
+            out["unpinned"] = [srv.result(i, r.shape[0], r.shape[-1]) for i, r in zip(ids, reqs[:6])]
+            assert srv.stats()["peak_device_bytes"] > 0
+        srv.close()
+    for (W1, V1, i1), (W2, V2, i2) in zip(out[True], out[False]):
+        assert torch.equal(W1, W2) and torch.equal(V1, V2) and torch.equal(i1, i2)
+    for (W1, V1, _), (W3, V3, _) in zip(out[True][:6], out["unpinned"]):
+        assert torch.equal(W1, W3) and torch.equal(V1, V3)
+
+
+@pytest.mark.parametrize("mode", ["batch", "fifo"])
+def test_native_server_refuses_requests_beyond_the_launch_cap(mode):
+    """A request larger than max_launch_matrices is refused before admission in both modes (its
+    descriptors would not fit the per-launch arrays)."""
+    srv = serve.NativeServer(budget_bytes=64 << 20, host_result_bytes=64 << 20, max_launch_matrices=8, mode=mode)
+    with pytest.raises(B.BedError, match="TOO_LARGE"):
+        srv.submit(torch.zeros(9, 8, 8))
+    rid = srv.submit(_requests(5, 1)[0][:8])
+    st, _, _, _ = B.bed_server_wait(srv.h, rid, 10.0)
+    assert st == B.BED_OK
+    srv.release(rid)
+    srv.close()
+
+
+def test_native_server_shutdown_completes_every_admitted_request():
+    """Requests queued right before destroy are launched and completed (the completion thread waits for
+    batches still being launched)."""
+    reqs = _requests(41, 40)
+    srv = serve.NativeServer(budget_bytes=256 << 20, host_result_bytes=256 << 20)
+    for r in reqs:
+        srv.submit(r)
+    srv.close()  # must return: every admitted launch is retired
