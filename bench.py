@@ -294,9 +294,16 @@ def run_ours(args, rank, world, local):
     side = {n: torch.cuda.Stream(dev) for n in SIZES}
     order = sorted(SIZES, reverse=True)  # the longest launch first
 
+    # every size with the team shape and leaf size the autotuner's table gives it (the same per-n choice
+    # the ragged kernel makes)
+    from paper_2604_27325_gb300 import autotune
+
+    tuning = autotune.load()
+    tuned = {n: autotune.uniform_params(n, tuning) for n in SIZES}
+
     def launch(n, s=None, params=None):
         st = B.bed_eigh_f32(Ad[n].data_ptr(), Wd[n].data_ptr(), Vd[n].data_ptr(), Id[n].data_ptr(), BATCH, n,
-                            params, (s or stream).cuda_stream)
+                            params if params is not None else tuned[n], (s or stream).cuda_stream)
         if st != B.BED_OK:
             raise B.BedError(B.bed_status_string(st) + " " + B.bed_last_cuda_error())
 
@@ -309,7 +316,7 @@ def run_ours(args, rank, world, local):
             s.wait_event(fork)
             if evs is not None:
                 evs[n][0].record(s)
-            launch(n, s, params)
+            launch(n, s, params[n] if isinstance(params, dict) else params)
             if evs is not None:
                 evs[n][1].record(s)
             join = torch.cuda.Event()
@@ -321,7 +328,7 @@ def run_ours(args, rank, world, local):
     for n in SIZES:
         cnt = torch.zeros(4, dtype=torch.int64, device=dev)
         st = B.bed_eigh_f32_counted(Ad[n].data_ptr(), Wd[n].data_ptr(), Vd[n].data_ptr(), Id[n].data_ptr(),
-                                    BATCH, n, None, cnt.data_ptr(), sp)
+                                    BATCH, n, tuned[n], cnt.data_ptr(), sp)
         assert st == B.BED_OK
         c = cnt.tolist()
         kbar[n] = c[2] / max(c[1], 1)
@@ -398,7 +405,8 @@ def run_ours(args, rank, world, local):
         per_n_how = "eager steps, each on an idle GPU, with an event pair around each launch"
 
     # variant: the merge products on the tensor cores (split-3xTF32), same step, timed the same way
-    tc_graph = capture_step(params=B.make_params(merge_tensor_cores=1))
+    tc_graph = capture_step(params={n: B.make_params(merge_tensor_cores=1, leaf_size=tuned[n].leaf_size)
+                                    for n in SIZES})
     for i in range(args.warmup):
         flush.fill_(float(i))
         tc_graph.replay()
@@ -444,9 +452,6 @@ def run_ours(args, rank, world, local):
 
     # the same 2048 matrices through the ragged persistent kernel (one ordering pass + one persistent
     # launch per step, replayed from a CUDA graph)
-    from paper_2604_27325_gb300 import autotune
-
-    tuning = autotune.load()
     u_ns = [n for n in SIZES for _ in range(BATCH)]
     u_rb = B.RaggedBatch(u_ns, device=dev, tuning=tuning).load([m for n in SIZES for m in inputs[n]])
     u_rb.capture()
@@ -476,8 +481,8 @@ def run_ours(args, rank, world, local):
         for n in sorted(groups, reverse=True):
             a, w, v = groups[n]
             g_side[n].wait_event(fork)
-            st = B.bed_eigh_f32(a.data_ptr(), w.data_ptr(), v.data_ptr(), None, a.shape[0], n, None,
-                                g_side[n].cuda_stream)
+            st = B.bed_eigh_f32(a.data_ptr(), w.data_ptr(), v.data_ptr(), None, a.shape[0], n,
+                                autotune.uniform_params(n, tuning), g_side[n].cuda_stream)
             if st != B.BED_OK:
                 raise B.BedError(B.bed_status_string(st))
             j = torch.cuda.Event()
@@ -503,8 +508,8 @@ def run_ours(args, rank, world, local):
         "persistent_graph": RAGGED_COUNT * world * K / (max_over_ranks(sum(rg_ms), world) / 1e3),
         "per_size_launches": RAGGED_COUNT * world * K / (max_over_ranks(sum(ps_ms), world) / 1e3),
         "per_size_launch_count": len(groups),
-        "per_size_how": "one launch per distinct n, each on its own stream (fork/join), the step replayed "
-                        "as one CUDA graph",
+        "per_size_how": "one launch per distinct n (team shape and leaf size from the autotuner table), each "
+                        "on its own stream (fork/join), the step replayed as one CUDA graph",
         "unit": "matrices/s",
     }
     ragged["speedup_vs_per_size"] = ragged["persistent_graph"] / ragged["per_size_launches"]
@@ -659,8 +664,8 @@ def run_ours(args, rank, world, local):
     best_uniform = max(value, uniform_via_ragged)
     launch = ("one ragged persistent launch (plus its one-block ordering pass) per step, CUDA-graph replay"
               if uniform_via_ragged > value else
-              "one launch per n, each on its own stream forked from and joined to the timing stream, the "
-              "step captured once as a CUDA graph and replayed")
+              "one launch per n (team shape and leaf size from the autotuner table), each on its own stream "
+              "forked from and joined to the timing stream, the step captured once as a CUDA graph and replayed")
     line = {
         "metric": METRIC, "value": best_uniform, "unit": "matrices/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -725,11 +730,16 @@ def run_ours(args, rank, world, local):
         summ["serve_2000"] = {k: [round(r0[m][k], 4) if r0[m].get(k) is not None else None
                                   for m in ("continuous_batching", "fifo_per_request_launches")]
                               for k in ("p50_ms", "p99_ms", "matrices_per_s")}
+        def _r(x, scale=1.0, nd=3):
+            return None if x is None else round(x / scale, nd)
+
+        # per offered rate: delivered M matrices/s and p99 ms, continuous batching then FIFO (null where
+        # FIFO was not run because it had already fallen behind at a lower rate)
         summ["serve_sweep_Mps_cb_fifo_p99ms"] = {
-            k: [round((v["continuous_batching"]["matrices_per_s"] or 0) / 1e6, 3),
-                round((v.get("fifo_per_request_launches", {}).get("matrices_per_s") or 0) / 1e6, 3),
-                round(v["continuous_batching"]["p99_ms"] or 0, 3),
-                round(v.get("fifo_per_request_launches", {}).get("p99_ms") or 0, 3)]
+            k: [_r(v["continuous_batching"]["matrices_per_s"], 1e6),
+                _r(v.get("fifo_per_request_launches", {}).get("matrices_per_s"), 1e6),
+                _r(v["continuous_batching"]["p99_ms"]),
+                _r(v.get("fifo_per_request_launches", {}).get("p99_ms"))]
             for k, v in serving["sweep"].items()}
     line["summary"] = summ
     if rank == 0:

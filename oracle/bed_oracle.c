@@ -17,7 +17,10 @@
  *   a3  Leaves: one Givens/Jacobi rotation per 2x2 block (Sec. 2.2); with a
  *       larger leaf size, blocks of 3..8 rows by the implicit QL iteration with
  *       Wilkinson shifts (the "batched QR" leaf option the paper mentions,
- *       Sec. 2.2; Golub & Van Loan Sec. 8.3, written in the QL direction).
+ *       Sec. 2.2). The step recurrence is the published one of the EISPACK
+ *       routine tql2 (Bowdler, Martin, Reinsch and Wilkinson, "The QR and QL
+ *       algorithms for symmetric matrices", Numer. Math. 11, 1968), also given
+ *       as tqli in Numerical Recipes; Golub & Van Loan Sec. 8.3 is the QR form.
  *   a4  Conquer: block spectral form Eq. (4) and coupling vector z Eq. (5);
  *       deflation (the paper does not describe it; Dongarra-Sorensen reading).
  *   a5  Secular equation Eq. (8) under the interlacing constraint Eq. (9)-(12):
@@ -229,7 +232,9 @@ void orc_eig2(double a, double b, double c, double* lam, double* Q)
 
 /*
  * a3 (larger leaves): eigendecomposition of the s x s tridiagonal (d, e) by the
- * implicit QL iteration with Wilkinson shifts. For the leading unreduced block
+ * implicit QL iteration with Wilkinson shifts, following the step recurrence
+ * of the EISPACK routine tql2 (Bowdler, Martin, Reinsch and Wilkinson 1968;
+ * tqli in Numerical Recipes). For the leading unreduced block
  * [l, mm] (mm the first index with a negligible e[mm]) one step chases the
  * bulge from the bottom: the shift is the eigenvalue of the top 2x2 block of
  * [l, mm] nearer to d[l], and rotations in planes (i, i+1), i = mm-1 .. l,

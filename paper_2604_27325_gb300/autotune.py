@@ -88,6 +88,16 @@ def load(path: str | None = None) -> B.bed_ragged_tuning:
     return t
 
 
+TEAM_THREADS = {0: 256, 1: 128, 2: 64, 3: 32, 4: 192}
+
+
+def uniform_params(n: int, tuning: B.bed_ragged_tuning | None = None) -> B.bed_params:
+    """Parameters of a uniform-size launch (bed_eigh_f32) with the team shape and leaf size the tuning
+    table gives size n, so that a uniform launch runs exactly what the ragged kernel would for n."""
+    t = tuning if tuning is not None else load()
+    return B.make_params(threads_per_matrix=TEAM_THREADS[int(t.team[n])], leaf_size=int(t.leaf[n]))
+
+
 if __name__ == "__main__":
     import sys
 

@@ -82,6 +82,28 @@ def test_ragged_equals_uniform_path_bitwise(team, n, leaf):
         assert torch.equal(res[k][0], W[k]) and torch.equal(res[k][1], V[k])
 
 
+@pytest.mark.parametrize("n48,n16,count48,count16", [(40, 12, 20, 30), (48, 16, 25, 9), (33, 5, 7, 7)])
+def test_mixed_team_classes_equal_uniform_path_bitwise(n48, n16, count48, count16):
+    """48-row-class and 16-row-class matrices in one ragged launch give bitwise the results of the
+    uniform launches of the same team shapes (192 and 64 threads)."""
+    A48 = wl.covariance(count48, n48, seed=700 + n48)
+    A16 = wl.known_spectrum(count16, n16, seed=800 + n16)[0]
+    ns = [n48] * count48 + [n16] * count16
+    rb = B.RaggedBatch(ns).load(list(A48) + list(A16)).solve()
+    torch.cuda.synchronize()
+    res = rb.results()
+    assert int((rb.info[: rb.count] != 0).sum()) == 0
+    for A, n, tpm, off in ((A48, n48, 192, 0), (A16, n16, 64, count48)):
+        Ad = torch.from_numpy(A).cuda()
+        W = torch.empty(A.shape[0], n, device="cuda")
+        V = torch.empty(A.shape[0], n, n, device="cuda")
+        assert B.bed_eigh_f32(Ad.data_ptr(), W.data_ptr(), V.data_ptr(), None, A.shape[0], n,
+                              B.make_params(threads_per_matrix=tpm), torch.cuda.current_stream().cuda_stream) == B.BED_OK
+        torch.cuda.synchronize()
+        for k in range(A.shape[0]):
+            assert torch.equal(res[off + k][0], W[k]) and torch.equal(res[off + k][1], V[k])
+
+
 def test_ragged_bad_sizes_are_flagged_and_skipped():
     ns = [8, 0, 12, 65, 3]
     rb = B.RaggedBatch(ns)
