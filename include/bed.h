@@ -264,6 +264,10 @@ bed_status bed_eigh_ragged_f32_noalloc(const float* A, const int64_t* offsets, c
  * separable eigenvectors), into gA [batch][n][n]. gA is the gradient over symmetric perturbations of A
  * (torch.linalg.eigh's convention). All pointers DEVICE memory; gW or gV may be NULL (zero gradient);
  * gA may not alias V. gap_eps >= 0 and finite. Same ownership, error and stream rules as bed_eigh_f32.
+ * gap_eps = 0 masks exact ties only. FP32 eigenvalues closer than about n * 2^-24 * max|W| cannot be
+ * told apart, and 1/(W_j - W_i) for such a pair is rounding noise of size up to 2^24 / (n max|W|):
+ * for inputs that may have (nearly) repeated eigenvalues pass a gap_eps of at least that size, e.g.
+ * 1e-6 * max|W| (the differentiation workload, with gaps >= 1e-3, needs none).
  */
 bed_status bed_eigh_backward_f32(const float* W, const float* V, const float* gW, const float* gV, float* gA,
                                  int64_t batch, int n, float gap_eps, cudaStream_t stream);

@@ -738,7 +738,10 @@ class EighFunction(torch.autograd.Function):
 def eigh(A: torch.Tensor, params: bed_params | None = None, gap_eps: float = 0.0):
     """Differentiable ``(W, V) = eigh(A)`` for a CUDA FP32 batch ``A[..., n, n]`` (lower triangle read).
     The gradient returned for A is symmetric (gradient over symmetric perturbations); eigenvalue pairs
-    closer than ``gap_eps`` do not couple their eigenvectors in the backward pass."""
+    closer than ``gap_eps`` do not couple their eigenvectors in the backward pass. The default 0 masks
+    exact ties only: for inputs that may have nearly repeated eigenvalues (closer than about
+    n * 2^-24 * max|lambda|, which FP32 cannot resolve) pass e.g. ``gap_eps = 1e-6 * max|lambda|``, or
+    the 1/gap factors of such pairs turn rounding noise into large gradients."""
     if not A.is_cuda:
         raise BedError("eigh (differentiable) expects a CUDA tensor")
     return EighFunction.apply(A, params, gap_eps)
