@@ -58,6 +58,7 @@ bool build_plan(int n, int leaf_size, Plan* P)
     for (int i = 0; i < P->nleaves; ++i) {
         P->leaf_lo[i] = static_cast<uint8_t>(leaves[2 * i]);
         P->leaf_hi[i] = static_cast<uint8_t>(leaves[2 * i + 1]);
+        P->max_leaf = std::max(P->max_leaf, leaves[2 * i + 1] - leaves[2 * i]);
     }
     int maxd = -1;
     for (const auto& m : merges) maxd = m.depth > maxd ? m.depth : maxd;

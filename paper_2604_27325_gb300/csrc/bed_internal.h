@@ -21,6 +21,7 @@ struct Plan {
     int nleaves;
     int nmerge;
     int nlevels;                            // merge levels; level 0 is the deepest
+    int max_leaf;                           // rows of the largest leaf
     unsigned long long cut_mask;            // bit t: the tridiagonal is torn between rows t and t+1
     uint8_t leaf_lo[kMaxN], leaf_hi[kMaxN]; // leaves [lo, hi), 1 to kMaxLeaf rows
     uint8_t m_lo[kMaxN], m_mid[kMaxN], m_hi[kMaxN];  // merges, grouped by level (deepest first)

@@ -255,10 +255,11 @@ constexpr uint64_t kDrainWaitNs = 2000000000ull;
 
 // ---------------------------------------------------------------------------------------------
 // a3 for leaves of 3..8 rows: implicit QL iteration with Wilkinson shifts (the small-block solver the
-// paper offers in place of dividing down to 2x2 blocks, Sec. 2.2). Every lane of a group of 8 runs
-// the same scalar recurrence on its own register copy of (d, e) -- no communication -- and applies
-// each plane rotation to its own row r of the leaf's eigenvector block. The loops are unrolled over
-// the 8 possible positions and predicated on the runtime bounds, so d, e and z stay in registers.
+// paper offers in place of dividing down to 2x2 blocks, Sec. 2.2; the step recurrence is the published
+// one of the EISPACK routine tql2). Every lane of a group of LM (4 or 8) runs the same scalar recurrence
+// on its own register copy of (d, e) -- no communication -- and applies each plane rotation to its own
+// row r of the leaf's eigenvector block. The loops are unrolled over the LM possible positions and
+// predicated on the runtime bounds, so d, e and z stay in registers.
 // Writes the eigenvalues (lane 0) and row r of the eigenvectors; returns false if an eigenvalue hit
 // the iteration cap.
 // ---------------------------------------------------------------------------------------------
@@ -275,12 +276,15 @@ __device__ __forceinline__ float selp(bool c, float a, float b)
 
 constexpr int kLeafMax = 8;
 
+// LM: the register arrays' length, at least the leaf's row count m. The unrolled steps cost LM positions
+// whatever m is, so leaves of up to 4 rows run the LM = 4 instance.
+template <int LM>
 __device__ __forceinline__ bool ql_leaf(const float* __restrict__ dg, const float* __restrict__ eg, int m,
                                         int r, float* __restrict__ lam_out, float* __restrict__ q_row)
 {
-    float d[kLeafMax], e[kLeafMax], z[kLeafMax];
+    float d[LM], e[LM], z[LM];
 #pragma unroll
-    for (int j = 0; j < kLeafMax; ++j) {
+    for (int j = 0; j < LM; ++j) {
         d[j] = (j < m) ? dg[j] : 0.f;
         e[j] = (j < m - 1) ? eg[j] : 0.f;
         z[j] = (j == r) ? 1.f : 0.f;
@@ -290,16 +294,16 @@ __device__ __forceinline__ bool ql_leaf(const float* __restrict__ dg, const floa
     // past every such coupling, so that the lanes of a warp (up to four leaves) advance together, one
     // step per pass, rather than waiting for each other at every eigenvalue.
     int l = 0, iter = 0;
-    for (int pass = 0; pass < 31 * kLeafMax; ++pass) {
+    for (int pass = 0; pass < 31 * LM; ++pass) {
         int mm = m - 1;
         {
-            bool negl[kLeafMax - 1];
+            bool negl[LM - 1];
 #pragma unroll
-            for (int j = 0; j < kLeafMax - 1; ++j)
+            for (int j = 0; j < LM - 1; ++j)
                 negl[j] = (j >= m - 1) || fabsf(e[j]) <= 0x1p-23f * (fabsf(d[j]) + fabsf(d[j + 1]));
             int ln = m - 1;
 #pragma unroll
-            for (int j = kLeafMax - 2; j >= 0; --j)
+            for (int j = LM - 2; j >= 0; --j)
                 if (j >= l && !negl[j]) ln = j;
             if (ln != l) iter = 0;
             l = ln;
@@ -313,13 +317,13 @@ __device__ __forceinline__ bool ql_leaf(const float* __restrict__ dg, const floa
             ++iter;
             // the first negligible coupling after l bounds the unreduced block [l, mm]
 #pragma unroll
-            for (int j = kLeafMax - 2; j >= 0; --j)
+            for (int j = LM - 2; j >= 0; --j)
                 if (j > l && j < m - 1 && negl[j]) mm = j;
         }
         {
             float dl = 0.f, dl1 = 0.f, el = 0.f, dmm = 0.f;
 #pragma unroll
-            for (int j = 0; j < kLeafMax; ++j) {
+            for (int j = 0; j < LM; ++j) {
                 dl = selp(j == l, d[j], dl);
                 el = selp(j == l, e[j], el);
                 dl1 = selp(j == l + 1, d[j], dl1);
@@ -333,7 +337,7 @@ __device__ __forceinline__ bool ql_leaf(const float* __restrict__ dg, const floa
             float sn = 1.f, cs = 1.f, p = 0.f;
             bool split = false;  // the bulge vanished: the block splits, the step ends early
 #pragma unroll
-            for (int i = kLeafMax - 2; i >= 0; --i) {
+            for (int i = LM - 2; i >= 0; --i) {
                 if (i < mm && i >= l && !split) {
                     const float f = sn * e[i], b = cs * e[i];
                     const float h2 = fmaf(f, f, g * g);
@@ -359,7 +363,7 @@ __device__ __forceinline__ bool ql_leaf(const float* __restrict__ dg, const floa
                 }
             }
 #pragma unroll
-            for (int j = 0; j < kLeafMax; ++j) {
+            for (int j = 0; j < LM; ++j) {
                 if (j == l && !split) {
                     d[j] -= p;
                     e[j] = g;
@@ -369,7 +373,7 @@ __device__ __forceinline__ bool ql_leaf(const float* __restrict__ dg, const floa
         }
     }
 #pragma unroll
-    for (int j = 0; j < kLeafMax; ++j)
+    for (int j = 0; j < LM; ++j)
         if (j < m) {
             if (r == 0) lam_out[j] = d[j];
             if (r < m) q_row[j] = z[j];
@@ -1099,12 +1103,27 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
     team_sync<NT>(bar_id);
 
     // ---------------- a3: leaves ------------------------------------------------------------
-    for (int lf = tid >> 3; lf < plan.nleaves; lf += NT >> 3) {
-        const int lo = plan.leaf_lo[lf], m = plan.leaf_hi[lf] - lo;
-        if (m >= 3) {
-            const int r = tid & 7;
-            const bool ok = ql_leaf(&S.d[lo], &S.e[lo], m, r, &S.lam[lo], &S.Q[(lo + min(r, m - 1)) * LD + lo]);
-            if (!ok && r == 0) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
+    // a leaf of m >= 3 rows is solved by a group of LM lanes (one per row of its eigenvector block),
+    // LM = 4 when every leaf of the tree has at most 4 rows, else 8
+    if (plan.max_leaf <= 4) {
+        for (int lf = tid >> 2; lf < plan.nleaves; lf += NT >> 2) {
+            const int lo = plan.leaf_lo[lf], m = plan.leaf_hi[lf] - lo;
+            if (m >= 3) {
+                const int r = tid & 3;
+                const bool ok =
+                    ql_leaf<4>(&S.d[lo], &S.e[lo], m, r, &S.lam[lo], &S.Q[(lo + min(r, m - 1)) * LD + lo]);
+                if (!ok && r == 0) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
+            }
+        }
+    } else {
+        for (int lf = tid >> 3; lf < plan.nleaves; lf += NT >> 3) {
+            const int lo = plan.leaf_lo[lf], m = plan.leaf_hi[lf] - lo;
+            if (m >= 3) {
+                const int r = tid & 7;
+                const bool ok =
+                    ql_leaf<8>(&S.d[lo], &S.e[lo], m, r, &S.lam[lo], &S.Q[(lo + min(r, m - 1)) * LD + lo]);
+                if (!ok && r == 0) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
+            }
         }
     }
     if (tid < plan.nleaves && plan.leaf_hi[tid] - plan.leaf_lo[tid] <= 2) {
