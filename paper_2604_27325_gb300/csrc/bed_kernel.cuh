@@ -1103,8 +1103,8 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
     team_sync<NT>(bar_id);
 
     // ---------------- a3: leaves ------------------------------------------------------------
-    // a leaf of m >= 3 rows is solved by a group of LM lanes (one per row of its eigenvector block),
-    // LM = 4 when every leaf of the tree has at most 4 rows, else 8
+    // a leaf of m >= 3 rows is solved by a group of lanes (one per row of its eigenvector block) with
+    // LM register slots: LM = 4 when every leaf of the tree has at most 4 rows, 6 for at most 6, else 8
     if (plan.max_leaf <= 4) {
         for (int lf = tid >> 2; lf < plan.nleaves; lf += NT >> 2) {
             const int lo = plan.leaf_lo[lf], m = plan.leaf_hi[lf] - lo;
@@ -1112,6 +1112,16 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 const int r = tid & 3;
                 const bool ok =
                     ql_leaf<4>(&S.d[lo], &S.e[lo], m, r, &S.lam[lo], &S.Q[(lo + min(r, m - 1)) * LD + lo]);
+                if (!ok && r == 0) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
+            }
+        }
+    } else if (plan.max_leaf <= 6) {
+        for (int lf = tid >> 3; lf < plan.nleaves; lf += NT >> 3) {
+            const int lo = plan.leaf_lo[lf], m = plan.leaf_hi[lf] - lo;
+            if (m >= 3) {
+                const int r = tid & 7;
+                const bool ok =
+                    ql_leaf<6>(&S.d[lo], &S.e[lo], m, r, &S.lam[lo], &S.Q[(lo + min(r, m - 1)) * LD + lo]);
                 if (!ok && r == 0) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
             }
         }
