@@ -62,8 +62,10 @@ enum {
  * defaults below. Passing NULL wherever a `const bed_params*` is taken means the defaults.
  */
 typedef struct {
-    int leaf_size;           /* divide (Sec. 2.1) until blocks have <= leaf_size rows, 1..8 (default 8);
-                                blocks of 3..8 rows are solved by the implicit QL iteration (Sec. 2.2) */
+    int leaf_size;           /* divide (Sec. 2.1) until blocks have <= leaf_size rows, 1..8, or 0 (default):
+                                automatic, a built-in per-n choice of 4 or 8 (and 2 for n = 2) measured by the
+                                autotuner on a GB300; blocks of 3..8 rows are solved by the implicit QL
+                                iteration (Sec. 2.2) */
     int k_multisection;      /* k of Eq. (16), >= 2 (default 4) */
     int max_section_iters;   /* cap on multi-section steps per root, 0..256 (default 24) */
     int max_halley_iters;    /* cap on Halley steps per root, 1..256 (default 32) */
@@ -198,7 +200,7 @@ typedef struct {
 } bed_ragged_tuning;
 
 /* Fills *t with the built-in choice: type 2 for n <= 16, type 1 for n <= 32, type 4 for n <= 48, type 0
- * above; leaf 8. */
+ * above; for each n the automatic leaf size of bed_params.leaf_size = 0. */
 void bed_ragged_default_tuning(bed_ragged_tuning* t);
 
 /* Bytes of device workspace bed_eigh_ragged_f32 needs for `count` matrices (a multiple of 256). */
@@ -360,7 +362,8 @@ const char* bed_last_cuda_error(void);
 
 /*
  * Host-side description of the divide tree the kernels follow for size n (Sec. 2.1: split at
- * floor(s/2) until blocks have <= leaf_size rows). Pure host logic, no CUDA call.
+ * floor(s/2) until blocks have <= leaf_size rows; leaf_size 0 = the automatic choice for n). Pure host
+ * logic, no CUDA call.
  *   merges  [3*64] receives (lo, mid, hi) of each merge, deepest level first (may be NULL)
  *   level_of[64]   receives the merge level (0 = deepest) of each merge (may be NULL)
  * Returns the number of merges (n - number of leaves), or -1 for an unsupported n / leaf_size.

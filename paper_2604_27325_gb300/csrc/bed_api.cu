@@ -83,9 +83,25 @@ bool build_plan(int n, int leaf_size, Plan* P)
     return true;
 }
 
+// Leaf size of the divide tree for leaf_size = 0 (automatic), by n: the autotuner's choice on a GB300
+// (per-n timing of every team shape and leaf size of 2, 4 and 8 rows, batch 2048; the team shapes it
+// chose are the built-in ones of bed_ragged_default_tuning). Leaves of up to 4 rows pay for 4 register
+// slots of the QL leaf solver, of 5-6 rows for 6 and of 7-8 for 8, so whether a deeper tree pays
+// depends on n.
+constexpr unsigned char kAutoLeaf[kMaxN + 1] = {
+    0, 4, 2, 8, 8, 8, 8, 4, 4, 8, 8, 8, 8, 4, 4, 4,
+    4, 4, 8, 8, 8, 8, 8, 8, 8, 4, 4, 4, 4, 4, 4, 4,
+    4, 4, 4, 4, 8, 8, 8, 8, 8, 8, 8, 8, 8, 8, 8, 8,
+    8, 8, 8, 8, 8, 8, 8, 8, 8, 4, 4, 4, 4, 4, 4, 4,
+    4,
+};
+
+int auto_leaf(int n) { return (n >= 1 && n <= kMaxN) ? kAutoLeaf[n] : 8; }
+
 // Divide trees of every n and leaf size, built once on first use (host memory, read-only afterwards).
 const Plan* cached_plan(int n, int leaf_size)
 {
+    if (leaf_size == 0) leaf_size = auto_leaf(n);
     static Plan plans[kMaxLeaf][kMaxN + 1];
     static bool ok[kMaxLeaf][kMaxN + 1];
     static std::once_flag once;
@@ -124,7 +140,7 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
 {
     bed_default_params(prm);
     if (p) *prm = *p;
-    if (prm->leaf_size < 1 || prm->leaf_size > kMaxLeaf) return false;
+    if (prm->leaf_size < 0 || prm->leaf_size > kMaxLeaf) return false;
     if (prm->k_multisection < 2 || prm->k_multisection > 64) return false;
     if (prm->max_section_iters < 0 || prm->max_section_iters > 256) return false;
     if (prm->max_halley_iters < 1 || prm->max_halley_iters > 256) return false;
@@ -228,7 +244,7 @@ void bed_ragged_default_tuning(bed_ragged_tuning* t)
     std::memset(t, 0, sizeof *t);
     for (int n = 0; n <= bed::kMaxN; ++n) {
         t->team[n] = static_cast<unsigned char>(n <= 16 ? 2 : (n <= 32 ? 1 : (n <= 48 ? 4 : 0)));
-        t->leaf[n] = 8;
+        t->leaf[n] = static_cast<unsigned char>(n >= 1 ? bed::auto_leaf(n) : 8);
     }
 }
 
@@ -267,7 +283,7 @@ bed_status bed_eigh_ragged_f32(const float* A, const int64_t* offsets, const int
 void bed_default_params(bed_params* p)
 {
     if (!p) return;
-    p->leaf_size = 8;
+    p->leaf_size = 0;
     p->k_multisection = 4;
     p->max_section_iters = 24;
     p->max_halley_iters = 32;
@@ -541,6 +557,7 @@ const char* bed_last_cuda_error(void) { return bed::g_last_cuda_error; }
 
 int bed_plan_describe(int n, int leaf_size, int* merges, int* level_of)
 {
+    if (leaf_size == 0) leaf_size = bed::auto_leaf(n);
     bed::Plan P;
     if (!bed::build_plan(n, leaf_size, &P)) return -1;
     for (int L = 0; L < P.nlevels; ++L)

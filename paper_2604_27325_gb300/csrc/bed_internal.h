@@ -44,6 +44,9 @@ struct KParams {
 
 bool build_plan(int n, int leaf_size, Plan* P);
 
+// Leaf size used for n when bed_params.leaf_size is 0 (automatic).
+int auto_leaf(int n);
+
 // One kernel launch over the whole batch. nmax in {16, 32, 64}, g in {2, 4} (threads = nmax * g).
 // bulk: stage each matrix with a TMA bulk copy (requires 16-byte aligned A and even n).
 cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int32_t* info,

@@ -36,7 +36,7 @@ def test_constants_and_strings():
     assert B.bed_status_string(99) == "BED_UNKNOWN_STATUS"
     assert C.sizeof(B.bed_counters) == 32
     p = B.bed_default_params()
-    assert (p.leaf_size, p.k_multisection, p.retire_by_vote, p.threads_per_matrix) == (8, 4, 1, 0)
+    assert (p.leaf_size, p.k_multisection, p.retire_by_vote, p.threads_per_matrix) == (0, 4, 1, 0)
     assert p.merge_tensor_cores == 0
     assert p.section_rel_eps == 2.0**-1
 
@@ -66,7 +66,7 @@ def test_empty_batch_is_ok_without_launch():
 
 @pytest.mark.parametrize(
     "field,value",
-    [("leaf_size", 9), ("leaf_size", 0), ("k_multisection", 1), ("max_halley_iters", 0),
+    [("leaf_size", 9), ("leaf_size", -1), ("k_multisection", 1), ("max_halley_iters", 0),
      ("max_section_iters", -1), ("section_rel_eps", 0.0), ("section_rel_eps", 1.0), ("stop_c", 0.5),
      ("deflation_tol_scale", 0.0), ("retire_by_vote", 2), ("threads_per_matrix", 100),
      ("merge_tensor_cores", 2), ("merge_tensor_cores", -1)],
@@ -106,7 +106,11 @@ def test_divide_tree_plan(leaf):
     with pytest.raises(ValueError):
         B.bed_plan_describe(8, 9)
     with pytest.raises(ValueError):
-        B.bed_plan_describe(8, 0)
+        B.bed_plan_describe(8, -1)
+    # leaf size 0: the automatic choice, a tree with leaves of at most 8 rows that every n has
+    for n in (2, 16, 33, 48, 64):
+        auto = B.bed_plan_describe(n, 0)
+        assert any(auto == B.bed_plan_describe(n, leaf) for leaf in (2, 4, 8))
 
 
 def test_no_cpu_fallback():
