@@ -72,7 +72,8 @@ typedef struct {
     float section_rel_eps;   /* Eq. (17): sectioning stops when U - L < eps * (initial bracket), (0,1) (default 2^-1) */
     float stop_c;            /* Halley stops when |f| <= stop_c * u * (1 + rho sum|z^2/(d - lambda)|), u = 2^-24 (default 8) */
     float deflation_tol_scale; /* deflation tolerance = scale * u * max(max|d|, rho |z|^2) (default 8) */
-    int threads_per_matrix;  /* 0 = automatic (4*nmax, nmax the smallest of {16, 32, 48, 64} that holds n);
+    int threads_per_matrix;  /* 0 = automatic (nmax the smallest of {16, 32, 48, 64} that holds n; 4*nmax
+                                threads, except 2*nmax = 128 for nmax = 64 unless merge_tensor_cores = 1);
                                 otherwise 2*nmax or 4*nmax for an nmax of that set with nmax >= n, the
                                 smallest such nmax when two match (64 = 4*16 or 2*32; 128 = 4*32 or 2*64) */
     int retire_by_vote;      /* 1 (default): a warp stops iterating secular roots as soon as all of its lanes

@@ -91,11 +91,13 @@ def load(path: str | None = None) -> B.bed_ragged_tuning:
 TEAM_THREADS = {0: 256, 1: 128, 2: 64, 3: 32, 4: 192}
 
 
-def uniform_params(n: int, tuning: B.bed_ragged_tuning | None = None) -> B.bed_params:
-    """Parameters of a uniform-size launch (bed_eigh_f32) with the team shape and leaf size the tuning
-    table gives size n, so that a uniform launch runs exactly what the ragged kernel would for n."""
+def uniform_params(n: int, tuning: B.bed_ragged_tuning | None = None, same_team: bool = False) -> B.bed_params:
+    """Parameters of a uniform-size launch (bed_eigh_f32) with the leaf size the tuning table gives size n
+    and the uniform kernel's automatic team shape; with ``same_team`` the team shape of the table too,
+    so that a uniform launch runs exactly (bitwise) what the ragged kernel would for n."""
     t = tuning if tuning is not None else load()
-    return B.make_params(threads_per_matrix=TEAM_THREADS[int(t.team[n])], leaf_size=int(t.leaf[n]))
+    tpm = TEAM_THREADS[int(t.team[n])] if same_team else 0
+    return B.make_params(threads_per_matrix=tpm, leaf_size=int(t.leaf[n]))
 
 
 if __name__ == "__main__":

@@ -166,10 +166,14 @@ namespace {
 
 // Team shape: nmax rows of tiles, G lanes per row; the smallest nmax that holds n unless the caller
 // asks for a thread count, which then selects the smallest (nmax >= n, G) with G * nmax equal to it.
+// Automatic: G = 4, except G = 2 for the 64-row team (128 threads with up to 128 registers each: half
+// the warps repeat the tridiagonalization's per-step vector work, and a warp's 16-column tile still
+// fits in registers; measured faster alone and beside the other sizes). The tensor-core merge variant
+// is instantiated for G = 4 only, so it keeps G = 4.
 bool team_shape(int n, const bed_params& prm, int* nmax_out, int* g_out)
 {
     int nmax = n <= 16 ? 16 : (n <= 32 ? 32 : (n <= 48 ? 48 : 64));
-    int g = 4;
+    int g = (nmax == 64 && !prm.merge_tensor_cores) ? 2 : 4;
     if (prm.threads_per_matrix != 0) {
         bool found = false;
         for (const int nm : {16, 32, 48, 64}) {
