@@ -1522,8 +1522,23 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             const int i = sub + G * t;
             q[t] = (pos < n && i < n) ? S.Q[i * LD + pos] : 0.f;
         }
+        // Rows i = sub + G t of this lane fall into PER classes of i & SW (the XOR swizzle of yt_index), so a
+        // block's two 16-byte chunks of row t sit at a class offset plus a compile-time row offset: the
+        // addresses cost a few instructions per block instead of per row
+        constexpr int CH = NMAX / 4;
+        constexpr int SWP = (CH % 8 == 0) ? 8 : ((CH % 4 == 0) ? 4 : ((CH % 2 == 0) ? 2 : 1));
+        constexpr int PER = SWP > G ? SWP / G : 1;
+        const float* Yrow = Yt + sub * NMAX;
+        const float* Wrow = Wt + sub * NMAX;
         for (int g = ngr - 1; g >= 0; --g) {
             const int k0 = g * kBT;
+            int offa[PER], offb[PER];  // yt_index(i, k0) - i NMAX and yt_index(i, k0 + 4) - i NMAX per class
+#pragma unroll
+            for (int c = 0; c < PER; ++c) {
+                const int sw = (sub + G * c) & (SWP - 1);
+                offa[c] = ((2 * g) ^ sw) << 2;
+                offb[c] = ((2 * g + 1) ^ sw) << 2;
+            }
             // W1 = Y^T q over this lane's rows; rows up to k0 are zero in every column of Y and W
             float w1[kBT];
 #pragma unroll
@@ -1531,9 +1546,8 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
 #pragma unroll
             for (int t = 0; t < RPT; ++t) {
                 if (G * t + G - 1 <= k0) continue;
-                const int i = sub + G * t;
-                const float4 ya = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0));
-                const float4 yb = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0 + 4));
+                const float4 ya = *reinterpret_cast<const float4*>(Yrow + G * t * NMAX + offa[t % PER]);
+                const float4 yb = *reinterpret_cast<const float4*>(Yrow + G * t * NMAX + offb[t % PER]);
                 w1[0] = fmaf(ya.x, q[t], w1[0]);
                 w1[1] = fmaf(ya.y, q[t], w1[1]);
                 w1[2] = fmaf(ya.z, q[t], w1[2]);
@@ -1549,9 +1563,8 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
 #pragma unroll
             for (int t = 0; t < RPT; ++t) {
                 if (G * t + G - 1 <= k0) continue;
-                const int i = sub + G * t;
-                const float4 wa = *reinterpret_cast<const float4*>(Wt + yt_index<NMAX>(i, k0));
-                const float4 wb = *reinterpret_cast<const float4*>(Wt + yt_index<NMAX>(i, k0 + 4));
+                const float4 wa = *reinterpret_cast<const float4*>(Wrow + G * t * NMAX + offa[t % PER]);
+                const float4 wb = *reinterpret_cast<const float4*>(Wrow + G * t * NMAX + offb[t % PER]);
                 float v = q[t];
                 v = fmaf(-wa.x, w1[0], v);
                 v = fmaf(-wa.y, w1[1], v);
