@@ -66,7 +66,7 @@ struct Smem {
     float brho[NB], btol[NB], bsc[NB];  // per merge of a level: |beta|, tolerance, scale
     int rank[NMAX];   // column c of the children -> its sorted position
     int inv[NMAX];    // compacted index -> sorted position
-    int org[NMAX];    // root -> compacted index of the pole it is measured from
+    float dorg[NMAX];  // root -> the (scaled) pole it is measured from, d_o
     int rotj[NMAX];   // sorted position -> rotation partner (-1: none)
     int defl[NMAX];
     int outc[NMAX];   // output column j <- column outc[j] of Q
@@ -1320,14 +1320,14 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             if (bt != 0xFF && q == 0 && tid % GS == 0) atomicAdd(&S.deflated, static_cast<unsigned>(hit - lot - K));
             const RootOut r = secular_root<GS>(S.cdz + lot, K, q, rho, kp, part, tid % GS);
             if (part && tid % GS == 0) {
-                S.org[t] = lot + r.org;
+                S.dorg[t] = S.cdz[lot + r.org].x;
                 S.tq[t] = r.tau;
                 S.lam[t] = (S.cdz[lot + r.org].x + r.tau) * (1.f / sc);
                 atomicAdd(&S.evals, static_cast<unsigned>(r.evals));
                 atomicAdd(&S.roots, 1u);
                 if (!r.conv) atomicOr(&S.info, BED_INFO_NOT_CONVERGED);
             } else if (bt != 0xFF && tid % GS == 0) {
-                S.org[t] = t;
+                S.dorg[t] = S.cdz[t].x;
                 S.tq[t] = 0.f;
                 S.lam[t] = S.cdz[t].x * (1.f / sc);
             }
@@ -1345,21 +1345,21 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             if (own) {
                 const float di = S.cdz[lo + i].x;
                 if (sub == 0)
-                    prod = ((S.cdz[S.org[lo + K - 1]].x - di) + S.tq[lo + K - 1]) / (S.brho[lb] * S.bsc[lb]);
+                    prod = ((S.dorg[lo + K - 1] - di) + S.tq[lo + K - 1]) / (S.brho[lb] * S.bsc[lb]);
                 // two ratios per division: their indices differ by G >= 2, so at most one of the two
                 // numerators is a root hugging d_i, and both products stay far inside the FP32 range
                 int j = sub;
 #pragma unroll 2
                 for (; j + G < K - 1; j += 2 * G) {
                     const int jb = j + G;
-                    const float na = (S.cdz[S.org[lo + j]].x - di) + S.tq[lo + j];  // lambda_j - d_i
-                    const float nb = (S.cdz[S.org[lo + jb]].x - di) + S.tq[lo + jb];
+                    const float na = (S.dorg[lo + j] - di) + S.tq[lo + j];  // lambda_j - d_i
+                    const float nb = (S.dorg[lo + jb] - di) + S.tq[lo + jb];
                     const float da = (j < i) ? (S.cdz[lo + j].x - di) : (S.cdz[lo + j + 1].x - di);
                     const float db = (jb < i) ? (S.cdz[lo + jb].x - di) : (S.cdz[lo + jb + 1].x - di);
                     prod *= (na * nb) * rcp_approx(da * db);
                 }
                 if (j < K - 1) {
-                    const float num = (S.cdz[S.org[lo + j]].x - di) + S.tq[lo + j];
+                    const float num = (S.dorg[lo + j] - di) + S.tq[lo + j];
                     const float den = (j < i) ? (S.cdz[lo + j].x - di) : (S.cdz[lo + j + 1].x - di);
                     prod *= num / den;
                 }
@@ -1378,7 +1378,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             float nrm2 = 0.f;
             if (act) {
                 if (q < K) {
-                    const float dorg = S.cdz[S.org[lo + q]].x;
+                    const float dorg = S.dorg[lo + q];
                     const float tq = S.tq[lo + q];
 #pragma unroll 4
                     for (int i = sub; i < K; i += G) {
