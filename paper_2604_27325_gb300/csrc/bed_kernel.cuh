@@ -453,10 +453,12 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
         if (!done) {
             const float dorg = dz[o].x;
             // four poles per pass (their loads and reciprocals in flight together), accumulated in two
-            // independent partial sums; then one pole at a time for the remainder
+            // independent partial sums, two passes unrolled so that the next pass's loads and
+            // reciprocals overlap this one's sums; then one pole at a time for the remainder
             if (deriv) {
                 float s0b = 0.f, s1b = 0.f, s2b = 0.f, sab = 0.f;
                 int j = sub;
+#pragma unroll 2
                 for (; j + 3 * G < K; j += 4 * G) {
                     const float2 pa = dz[j], pb = dz[j + G], pc = dz[j + 2 * G], pd = dz[j + 3 * G];
                     const float ia = rcp_approx((pa.x - dorg) - h), ib = rcp_approx((pb.x - dorg) - h);
@@ -489,6 +491,7 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
             } else {
                 float s0b = 0.f, s0c = 0.f, s0d = 0.f;
                 int j = sub;
+#pragma unroll 2
                 for (; j + 3 * G < K; j += 4 * G) {
                     const float2 pa = dz[j], pb = dz[j + G], pc = dz[j + 2 * G], pd = dz[j + 3 * G];
                     s0 = fmaf(pa.y, rcp_approx((pa.x - dorg) - h), s0);
@@ -1449,6 +1452,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
 #pragma unroll
                 for (int m = 0; m < (NMAX + 31) / 32; ++m) {
                     const int i = lane + 32 * m;
+                    if (32 * m + 31 <= k0) continue;  // rows up to k0 are zero in Y
                     if (i < NMAX) {
                         const float4 ya = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0));
                         const float4 yb = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0 + 4));
@@ -1493,6 +1497,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
 #pragma unroll
             for (int m = 0; m < (NMAX + 31) / 32; ++m) {
                 const int i = lane + 32 * m;
+                if (32 * m + 31 < k0) continue;  // rows below k0 of W are never read
                 float y[kBT] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 if (i < NMAX) {
                     const float4 ya = *reinterpret_cast<const float4*>(Yt + yt_index<NMAX>(i, k0));
@@ -1539,41 +1544,51 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 offa[c] = ((2 * g) ^ sw) << 2;
                 offb[c] = ((2 * g + 1) ^ sw) << 2;
             }
-            // W1 = Y^T q over this lane's rows; rows up to k0 are zero in every column of Y and W
+            // W1 = Y^T q over this lane's rows; rows up to k0 are zero in every column of Y and W. The
+            // rows go in chunks of 8 (TPC values of t): a chunk wholly above row k0 is skipped by a test
+            // that is the same on every lane, so its loads and FMAs are not issued at all (a test per
+            // row would only predicate them off)
+            constexpr int TPC = 8 / G;
             float w1[kBT];
 #pragma unroll
             for (int r = 0; r < kBT; ++r) w1[r] = 0.f;
 #pragma unroll
-            for (int t = 0; t < RPT; ++t) {
-                if (G * t + G - 1 <= k0) continue;
-                const float4 ya = *reinterpret_cast<const float4*>(Yrow + G * t * NMAX + offa[t % PER]);
-                const float4 yb = *reinterpret_cast<const float4*>(Yrow + G * t * NMAX + offb[t % PER]);
-                w1[0] = fmaf(ya.x, q[t], w1[0]);
-                w1[1] = fmaf(ya.y, q[t], w1[1]);
-                w1[2] = fmaf(ya.z, q[t], w1[2]);
-                w1[3] = fmaf(ya.w, q[t], w1[3]);
-                w1[4] = fmaf(yb.x, q[t], w1[4]);
-                w1[5] = fmaf(yb.y, q[t], w1[5]);
-                w1[6] = fmaf(yb.z, q[t], w1[6]);
-                w1[7] = fmaf(yb.w, q[t], w1[7]);
+            for (int c8 = 0; c8 < RPT / TPC; ++c8) {
+                if (8 * c8 + 7 <= k0) continue;
+#pragma unroll
+                for (int t = c8 * TPC; t < c8 * TPC + TPC; ++t) {
+                    const float4 ya = *reinterpret_cast<const float4*>(Yrow + G * t * NMAX + offa[t % PER]);
+                    const float4 yb = *reinterpret_cast<const float4*>(Yrow + G * t * NMAX + offb[t % PER]);
+                    w1[0] = fmaf(ya.x, q[t], w1[0]);
+                    w1[1] = fmaf(ya.y, q[t], w1[1]);
+                    w1[2] = fmaf(ya.z, q[t], w1[2]);
+                    w1[3] = fmaf(ya.w, q[t], w1[3]);
+                    w1[4] = fmaf(yb.x, q[t], w1[4]);
+                    w1[5] = fmaf(yb.y, q[t], w1[5]);
+                    w1[6] = fmaf(yb.z, q[t], w1[6]);
+                    w1[7] = fmaf(yb.w, q[t], w1[7]);
+                }
             }
 #pragma unroll
             for (int r = 0; r < kBT; ++r) w1[r] = gsum<G>(w1[r]);
-            // q -= W W1
+            // q -= W W1, over the same chunks
 #pragma unroll
-            for (int t = 0; t < RPT; ++t) {
-                if (G * t + G - 1 <= k0) continue;
-                const float4 wa = *reinterpret_cast<const float4*>(Wrow + G * t * NMAX + offa[t % PER]);
-                const float4 wb = *reinterpret_cast<const float4*>(Wrow + G * t * NMAX + offb[t % PER]);
-                float v = q[t];
-                v = fmaf(-wa.x, w1[0], v);
-                v = fmaf(-wa.y, w1[1], v);
-                v = fmaf(-wa.z, w1[2], v);
-                v = fmaf(-wa.w, w1[3], v);
-                v = fmaf(-wb.x, w1[4], v);
-                v = fmaf(-wb.y, w1[5], v);
-                v = fmaf(-wb.z, w1[6], v);
-                q[t] = fmaf(-wb.w, w1[7], v);
+            for (int c8 = 0; c8 < RPT / TPC; ++c8) {
+                if (8 * c8 + 7 <= k0) continue;
+#pragma unroll
+                for (int t = c8 * TPC; t < c8 * TPC + TPC; ++t) {
+                    const float4 wa = *reinterpret_cast<const float4*>(Wrow + G * t * NMAX + offa[t % PER]);
+                    const float4 wb = *reinterpret_cast<const float4*>(Wrow + G * t * NMAX + offb[t % PER]);
+                    float v = q[t];
+                    v = fmaf(-wa.x, w1[0], v);
+                    v = fmaf(-wa.y, w1[1], v);
+                    v = fmaf(-wa.z, w1[2], v);
+                    v = fmaf(-wa.w, w1[3], v);
+                    v = fmaf(-wb.x, w1[4], v);
+                    v = fmaf(-wb.y, w1[5], v);
+                    v = fmaf(-wb.z, w1[6], v);
+                    q[t] = fmaf(-wb.w, w1[7], v);
+                }
             }
         }
 #pragma unroll
@@ -1629,8 +1644,28 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         }
     }
     team_sync<NT>(bar_id);
-    for (int i = warp; i < n; i += NW)
-        for (int j = lane; j < n; j += 32) S.out_v[i * n + j] = S.sgn[j] * S.Q[i * LD + S.outc[j]];
+    {
+        // each lane stores the same output columns j = lane + 32 t of every row: their signs and source
+        // columns are read once
+        constexpr int JPL = (NMAX + 31) / 32;
+        float sj[JPL];
+        int cj[JPL];
+#pragma unroll
+        for (int t = 0; t < JPL; ++t) {
+            const int j = lane + 32 * t;
+            sj[t] = (j < n) ? S.sgn[j] : 0.f;
+            cj[t] = (j < n) ? S.outc[j] : 0;
+        }
+        float* ov = S.out_v;
+        for (int i = warp; i < n; i += NW) {
+            const float* qi = S.Q + i * LD;
+#pragma unroll
+            for (int t = 0; t < JPL; ++t) {
+                const int j = lane + 32 * t;
+                if (j < n) ov[i * n + j] = sj[t] * qi[cj[t]];
+            }
+        }
+    }
     if (tid == 0) {
         if (S.out_info) *S.out_info = S.info;
         if (counters) {
