@@ -663,8 +663,8 @@ __device__ __forceinline__ void mbar_init(uint32_t bar)
 }
 
 // a7 on the FP32 FMA pipes. Register tiles: the rows of one half of a merge times its columns form a
-// small product over the half's columns c. The level's tiles (PR rows x PC columns, merges in order, row
-// tiles of the left half, then of the right half, each with all column tiles) are dealt one per thread;
+// small product over the half's columns c. The level's tiles (PR rows x PC columns, merges in order, the
+// left half's tiles, then the right half's, each half column tile by column tile) are dealt one per thread;
 // per c a thread reads PR entries of Q, one row of Q^ (PC entries) and does PR x PC FMAs. The products
 // are scaled by the reciprocal column norms of Q^ when stored (after the team barrier: Q is read by all).
 template <int NMAX, int G>
@@ -684,10 +684,15 @@ __device__ __forceinline__ void merge_product_fma(Smem<NMAX, G>& S, const Plan& 
             const int ctn = (hi - lo + PC - 1) / PC;
             const int cnt = (rtl + rtr) * ctn;
             if (tid >= tbase && tid < tbase + cnt) {
+                // a half's tiles are dealt down its row tiles first: the lanes of a warp then span
+                // more row tiles and fewer column tiles, so that a warp's reads of one row of Q^ fall in
+                // distinct banks
                 const int u = tid - tbase;
-                const int rr = u / ctn, ct = u - rr * ctn;
-                const bool left = rr < rtl;
-                r0 = left ? lo + PR * rr : md + PR * (rr - rtl);
+                const bool left = u < rtl * ctn;
+                const int uh = left ? u : u - rtl * ctn;
+                const int rth = left ? rtl : rtr;
+                const int ct = uh / rth, rr = uh - ct * rth;
+                r0 = left ? lo + PR * rr : md + PR * rr;
                 rend = left ? md : hi;
                 c0 = left ? lo : md;
                 c1 = left ? md : hi;
