@@ -809,6 +809,236 @@ __device__ __forceinline__ void merge_product_tc(Smem<NMAX, G>& S, const Plan& p
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// a1 in phases of 16 steps. Rows below step k are finished, so phase p (steps 16 p .. 16 p + 15) keeps
+// only rows 16 p .. NMAX - 1 of its warp's columns in registers: TRP = (NMAX - 16 p) / 16 rows per lane,
+// rows r0 + TRP tr + [0, TRP) with r0 = 16 p. Between phases a warp moves its tile to the smaller shape
+// through the staging area (free during a1), so every later step updates and sums fewer rows.
+// ---------------------------------------------------------------------------------------------
+template <int NMAX, int G>
+__host__ __device__ constexpr int a1_tile_cols()
+{
+    return (NMAX / (NMAX * G / 32)) / a1_col_lanes<NMAX, G>();
+}
+
+// steps k0 .. k1 - 1 with the rows r0 .. NMAX - 1 in registers
+template <int NMAX, int G, int TRP>
+__device__ __forceinline__ void a1_steps(Smem<NMAX, G>& S, float (&a)[TRP][a1_tile_cols<NMAX, G>()], int r0,
+                                         int k0, int k1, int n, float& tau_prev, int tid, int bar_id)
+{
+    constexpr int NT = NMAX * G;
+    constexpr int NW = NT / 32;
+    constexpr int WC = NMAX / NW;
+    constexpr int NTC = a1_col_lanes<NMAX, G>();
+    constexpr int TC = a1_tile_cols<NMAX, G>();
+    constexpr int LOG_TC = ilog2(TC);
+    constexpr int LOG_NTC = ilog2(NTC);
+    const int lane = tid & 31, warp = tid >> 5;
+    const int tr = lane / NTC, tc = lane % NTC;
+    const int i0 = r0 + tr * TRP, j0 = warp * WC + tc * TC;
+    const int wlast = (n - 1) / WC;  // owns column n - 1: active in every step; stores reflectors
+    for (int k = k0; k < k1; ++k) {
+        const float* Pr = S.hp[(k + 1) & 1];
+        const float* Ur = S.hu[(k + 1) & 1];
+        const float* Yr = S.hy[(k + 1) & 1];
+        float tau = 0.f;
+        if (warp * WC + WC > k + 1 && warp <= wlast) {
+            // the three vectors on this lane's rows; every warp holds all rows from r0, so sums over
+            // rows are sums over the 16 row lanes (the two column lanes of a row agree). v_{k-1} is
+            // zero on the rows below r0 <= k, which therefore add nothing to p.v
+            float pr[TRP], ur[TRP], yr[TRP];
+            load_vec<TRP>(Pr + i0, pr);
+            load_vec<TRP>(Ur + i0, ur);
+            load_vec<TRP>(Yr + i0, yr);
+            float dot = 0.f;
+#pragma unroll
+            for (int ii = 0; ii < TRP; ++ii) dot = fmaf(pr[ii], ur[ii], dot);
+            const float c = 0.5f * tau_prev * row_lane_sum<NTC>(dot);  // (tau/2) p.v of step k - 1
+            const float uk = Ur[k];
+            const float wk = fmaf(-c, uk, Pr[k]);
+            if (warp == wlast && lane == 0) S.d[k] = fmaf(-2.f * uk, wk, Yr[k]);
+            // w of step k - 1 and x = column k of the updated matrix. v_{k-1} is zero on the
+            // finished rows i < k, so the update below leaves the active block exact without
+            // masking; the finished rows and columns pick up bounded values that no later step
+            // reads (the column sums and x are taken against v_k, zero there). Rows >= n stay zero.
+            float wr[TRP], xr[TRP];
+            float part = 0.f;
+#pragma unroll
+            for (int ii = 0; ii < TRP; ++ii) {
+                const int i = i0 + ii;
+                wr[ii] = fmaf(-c, ur[ii], pr[ii]);
+                xr[ii] = fmaf(-wr[ii], uk, fmaf(-ur[ii], wk, yr[ii]));
+                if (i > k + 1) part = fmaf(xr[ii], xr[ii], part);
+            }
+            // the update of step k - 1 needs only c: apply it to the tile (rows and columns >= k)
+            // while the reduction for reflector k is in flight
+            float pc[TC], uc[TC];
+            load_vec<TC>(Pr + j0, pc);
+            load_vec<TC>(Ur + j0, uc);
+#pragma unroll
+            for (int jj = 0; jj < TC; ++jj) {
+                const float u = uc[jj];
+                const float w = fmaf(-c, u, pc[jj]);
+#pragma unroll
+                for (int ii = 0; ii < TRP; ++ii) a[ii][jj] = fmaf(-ur[ii], w, fmaf(-wr[ii], u, a[ii][jj]));
+            }
+            // column k + 1 of the updated matrix, for step k + 1
+            if (warp == (k + 1) / WC && tc == ((k + 1) % WC) / TC) {
+                const int kj = (k + 1) % TC;
+                float yk[TRP];
+#pragma unroll
+                for (int ii = 0; ii < TRP; ++ii) {
+                    float x = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < TC; ++jj) x = (jj == kj) ? a[ii][jj] : x;
+                    yk[ii] = x;
+                }
+                store_vec<TRP>(S.hy[k & 1] + i0, yk);
+            }
+            const float xn2 = row_lane_sum<NTC>(part);
+            const float u1 = Ur[k + 1];
+            const float alpha = fmaf(-fmaf(-c, u1, Pr[k + 1]), uk, fmaf(-u1, wk, Yr[k + 1]));
+            // reflector k; when x is already zero below its first entry, tau = 0 and beta = alpha.
+            // |beta| = nrm and |alpha - beta| >= nrm: both normal, far from overflow
+            const float nrm = sqrt_approx(fmaf(alpha, alpha, xn2));
+            const bool refl = xn2 > 0.f;
+            const float beta = refl ? ((alpha >= 0.f) ? -nrm : nrm) : alpha;
+            tau = refl ? (beta - alpha) * rcp_approx(beta) : 0.f;
+            const float scal = refl ? rcp_approx(alpha - beta) : 0.f;
+            float vr[TRP];
+#pragma unroll
+            for (int ii = 0; ii < TRP; ++ii) {
+                const int i = i0 + ii;
+                vr[ii] = (i > k + 1) ? xr[ii] * scal : ((i == k + 1) ? 1.f : 0.f);
+            }
+            // reflector k: for the next step and, transposed, for the back-transform (its rows
+            // below r0 are zero and stay as a1 cleared them)
+            if (warp == wlast && tc == 0) {
+                store_vec<TRP>(S.hu[k & 1] + i0, vr);
+#pragma unroll
+                for (int ii = 0; ii < TRP; ++ii) S.A[yt_index<NMAX>(i0 + ii, k)] = vr[ii];
+                if (lane == 0) {
+                    S.e[k] = beta;
+                    S.tau[k] = tau;
+                }
+            }
+            // column sums of the updated tile with v_k
+            float s[TC];
+#pragma unroll
+            for (int jj = 0; jj < TC; ++jj) {
+                float acc = 0.f;
+#pragma unroll
+                for (int ii = 0; ii < TRP; ++ii) acc = fmaf(a[ii][jj], vr[ii], acc);
+                s[jj] = acc;
+            }
+            // sum over the row lanes: halving exchanges leave the lowest LOG_TC row-lane bits
+            // holding one column each, plain butterflies finish the sum
+            int cb = 0;
+#pragma unroll
+            for (int l = 0; l < LOG_TC; ++l) {
+                const int h = TC >> (l + 1);
+                const int o = NTC << l;
+                const bool up = (lane & o) != 0;
+#pragma unroll
+                for (int t = 0; t < h; ++t) {
+                    const float send = up ? s[t] : s[t + h];
+                    const float keep = up ? s[t + h] : s[t];
+                    s[t] = keep + __shfl_xor_sync(kFull, send, o);
+                }
+                if (up) cb += h;
+            }
+#pragma unroll
+            for (int o = NTC << LOG_TC; o < 32; o <<= 1) s[0] += __shfl_xor_sync(kFull, s[0], o);
+            float* Pw = S.hp[k & 1];
+            if ((lane >> (LOG_NTC + LOG_TC)) == 0) Pw[j0 + cb] = tau * s[0];
+        }
+        tau_prev = tau;
+        team_sync<NT>(bar_id);
+    }
+}
+
+// the trailing 2 x 2 block after the last update (the whole matrix when n <= 2), from the tile of the
+// last phase (rows r0 .. NMAX - 1, r0 <= n - 2)
+template <int NMAX, int G, int TRP>
+__device__ __forceinline__ void a1_last(Smem<NMAX, G>& S, const float (&a)[TRP][a1_tile_cols<NMAX, G>()],
+                                        int r0, int n, float tau_prev, int tid)
+{
+    constexpr int NW = NMAX * G / 32;
+    constexpr int WC = NMAX / NW;
+    constexpr int NTC = a1_col_lanes<NMAX, G>();
+    constexpr int TC = a1_tile_cols<NMAX, G>();
+    const int lane = tid & 31, warp = tid >> 5;
+    const int tr = lane / NTC, tc = lane % NTC;
+    const int i0 = r0 + tr * TRP, j0 = warp * WC + tc * TC;
+    const int wlast = (n - 1) / WC;
+    const int kf = n - 2;
+    if (n >= 2 && warp * WC + WC > kf && warp <= wlast) {
+        const float* Pr = S.hp[(kf + 1) & 1];
+        const float* Ur = S.hu[(kf + 1) & 1];
+        float dot = 0.f;
+#pragma unroll
+        for (int ii = 0; ii < TRP; ++ii) dot = fmaf(Pr[i0 + ii], Ur[i0 + ii], dot);
+        const float c = 0.5f * tau_prev * row_lane_sum<NTC>(dot);
+#pragma unroll
+        for (int ii = 0; ii < TRP; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < TC; ++jj) {
+                const int i = i0 + ii, j = j0 + jj;
+                if (i >= kf && j >= kf && i < n && j < n && j <= i) {
+                    const float ui = Ur[i], uj = Ur[j];
+                    const float wi = fmaf(-c, ui, Pr[i]), wj = fmaf(-c, uj, Pr[j]);
+                    const float x = fmaf(-ui, wj, fmaf(-wi, uj, a[ii][jj]));
+                    if (i == j) S.d[i] = x;
+                    else S.e[kf] = x;
+                }
+            }
+    } else if (n == 1 && tid == 0) {
+        S.d[0] = a[0][0];
+    }
+}
+
+// phase r0 / 16 and the ones after it
+template <int NMAX, int G, int TRP>
+__device__ __forceinline__ void a1_run(Smem<NMAX, G>& S, float (&a)[TRP][a1_tile_cols<NMAX, G>()], int r0, int n,
+                                       float& tau_prev, int tid, int bar_id)
+{
+    constexpr int NW = NMAX * G / 32;
+    constexpr int WC = NMAX / NW;
+    constexpr int NTC = a1_col_lanes<NMAX, G>();
+    constexpr int TC = a1_tile_cols<NMAX, G>();
+    constexpr int LD = Smem<NMAX, G>::LD;
+    const int ks = n - 2;  // steps k = 0 .. n - 3
+    if constexpr (TRP > 1) {
+        if (ks > r0 + 16) {
+            a1_steps<NMAX, G, TRP>(S, a, r0, r0, r0 + 16, n, tau_prev, tid, bar_id);
+            // rows r0 + 16 .. of this warp's columns to the next phase's layout, through the staging
+            // area (each warp moves only its own columns)
+            const int lane = tid & 31, warp = tid >> 5;
+            const int tr = lane / NTC, tc = lane % NTC;
+            const int j0 = warp * WC + tc * TC;
+#pragma unroll
+            for (int ii = 0; ii < TRP; ++ii) {
+                const int i = r0 + tr * TRP + ii;
+                if (i >= r0 + 16)
+#pragma unroll
+                    for (int jj = 0; jj < TC; ++jj) S.M[i * LD + j0 + jj] = a[ii][jj];
+            }
+            __syncwarp();
+            float b[TRP - 1][TC];
+#pragma unroll
+            for (int ii = 0; ii < TRP - 1; ++ii) {
+                const int i = r0 + 16 + tr * (TRP - 1) + ii;
+#pragma unroll
+                for (int jj = 0; jj < TC; ++jj) b[ii][jj] = S.M[i * LD + j0 + jj];
+            }
+            a1_run<NMAX, G, TRP - 1>(S, b, r0 + 16, n, tau_prev, tid, bar_id);
+            return;
+        }
+    }
+    a1_steps<NMAX, G, TRP>(S, a, r0, r0, ks, n, tau_prev, tid, bar_id);
+    a1_last<NMAX, G, TRP>(S, a, r0, n, tau_prev, tid);
+}
+
 template <int NMAX, int G, bool TC = false>
 __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan, const KParams& kp, const int tid,
                                              const int bar_id, const uint32_t bar, uint32_t& phase,
@@ -917,7 +1147,9 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
     // forms, redundantly and identically, w_{k-1} = p - (tau/2)(p.v) v, column k of the updated matrix
     // and reflector k (each warp holds every row, so the sums over rows are shuffle sums over its row
     // lanes); it applies A22 -= v w^T + w v^T of step k-1 to its tile and forms the column sums with
-    // v_k. A warp whose columns are all finished skips the step.
+    // v_k. A warp whose columns are all finished skips the step. The steps run in phases of 16 (a1_run):
+    // rows below the phase's first step are finished, so each phase keeps 16 rows fewer per column
+    // (the tile starts with all NMAX rows, TR per lane).
     {
         constexpr int WC = NMAX / NW;             // columns per warp
         constexpr int NTC = a1_col_lanes<NMAX, G>();  // lanes along the columns
@@ -927,7 +1159,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         constexpr int LOG_TC = ilog2(TC);
         constexpr int LOG_NTC = ilog2(NTC);
         static_assert(WC * NW == NMAX && TR * NTR == NMAX && TC * NTC == WC && (1 << LOG_TC) == TC &&
-                          (1 << LOG_NTC) == NTC,
+                          (1 << LOG_NTC) == NTC && NTR == 16 && TC == a1_tile_cols<NMAX, G>(),
                       "tile shape");
         const int tr = lane / NTC, tc = lane % NTC;
         const int i0 = tr * TR, j0 = warp * WC + tc * TC;
@@ -949,154 +1181,16 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             S.hu[1][i] = 0.f;
             S.hy[1][i] = (i < n) ? S.M[i * n] * scale : 0.f;
         }
+        // the reflectors' rows above each phase are not stored by the steps: they start out zero
+        for (int i = tid; i < NMAX * NMAX / 4; i += NT)
+            reinterpret_cast<float4*>(S.A)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         team_sync<NT>(bar_id);  // every tile is loaded before the merge phases reuse the staging area
-        const int wlast = (n - 1) / WC;  // owns column n - 1: active in every step; stores reflectors
         float tau_prev = 0.f;
-        for (int k = 0; k + 2 < n; ++k) {
-            const float* Pr = S.hp[(k + 1) & 1];
-            const float* Ur = S.hu[(k + 1) & 1];
-            const float* Yr = S.hy[(k + 1) & 1];
-            float tau = 0.f;
-            if (warp * WC + WC > k + 1 && warp <= wlast) {
-                // the three vectors on this lane's rows; every warp holds all NMAX rows, so sums over
-                // rows are sums over the 16 row lanes (the two column lanes of a row agree)
-                float pr[TR], ur[TR], yr[TR];
-                load_vec<TR>(Pr + i0, pr);
-                load_vec<TR>(Ur + i0, ur);
-                load_vec<TR>(Yr + i0, yr);
-                float dot = 0.f;
-#pragma unroll
-                for (int ii = 0; ii < TR; ++ii) dot = fmaf(pr[ii], ur[ii], dot);
-                const float c = 0.5f * tau_prev * row_lane_sum<NTC>(dot);  // (tau/2) p.v of step k - 1
-                const float uk = Ur[k];
-                const float wk = fmaf(-c, uk, Pr[k]);
-                if (warp == wlast && lane == 0) S.d[k] = fmaf(-2.f * uk, wk, Yr[k]);
-                // w of step k - 1 and x = column k of the updated matrix. v_{k-1} is zero on the
-                // finished rows i < k, so the update below leaves the active block exact without
-                // masking; the finished rows and columns pick up bounded values that no later step
-                // reads (the column sums and x are taken against v_k, zero there). Rows >= n stay zero.
-                float wr[TR], xr[TR];
-                float part = 0.f;
-#pragma unroll
-                for (int ii = 0; ii < TR; ++ii) {
-                    const int i = i0 + ii;
-                    wr[ii] = fmaf(-c, ur[ii], pr[ii]);
-                    xr[ii] = fmaf(-wr[ii], uk, fmaf(-ur[ii], wk, yr[ii]));
-                    if (i > k + 1) part = fmaf(xr[ii], xr[ii], part);
-                }
-                // the update of step k - 1 needs only c: apply it to the tile (rows and columns >= k)
-                // while the reduction for reflector k is in flight
-                float pc[TC], uc[TC];
-                load_vec<TC>(Pr + j0, pc);
-                load_vec<TC>(Ur + j0, uc);
-#pragma unroll
-                for (int jj = 0; jj < TC; ++jj) {
-                    const float u = uc[jj];
-                    const float w = fmaf(-c, u, pc[jj]);
-#pragma unroll
-                    for (int ii = 0; ii < TR; ++ii) a[ii][jj] = fmaf(-ur[ii], w, fmaf(-wr[ii], u, a[ii][jj]));
-                }
-                // column k + 1 of the updated matrix, for step k + 1
-                if (warp == (k + 1) / WC && tc == ((k + 1) % WC) / TC) {
-                    const int kj = (k + 1) % TC;
-                    float yk[TR];
-#pragma unroll
-                    for (int ii = 0; ii < TR; ++ii) {
-                        float x = 0.f;
-#pragma unroll
-                        for (int jj = 0; jj < TC; ++jj) x = (jj == kj) ? a[ii][jj] : x;
-                        yk[ii] = x;
-                    }
-                    store_vec<TR>(S.hy[k & 1] + i0, yk);
-                }
-                const float xn2 = row_lane_sum<NTC>(part);
-                const float u1 = Ur[k + 1];
-                const float alpha = fmaf(-fmaf(-c, u1, Pr[k + 1]), uk, fmaf(-u1, wk, Yr[k + 1]));
-                // reflector k; when x is already zero below its first entry, tau = 0 and beta = alpha.
-                // |beta| = nrm and |alpha - beta| >= nrm: both normal, far from overflow
-                const float nrm = sqrt_approx(fmaf(alpha, alpha, xn2));
-                const bool refl = xn2 > 0.f;
-                const float beta = refl ? ((alpha >= 0.f) ? -nrm : nrm) : alpha;
-                tau = refl ? (beta - alpha) * rcp_approx(beta) : 0.f;
-                const float scal = refl ? rcp_approx(alpha - beta) : 0.f;
-                float vr[TR];
-#pragma unroll
-                for (int ii = 0; ii < TR; ++ii) {
-                    const int i = i0 + ii;
-                    vr[ii] = (i > k + 1) ? xr[ii] * scal : ((i == k + 1) ? 1.f : 0.f);
-                }
-                // reflector k: for the next step and, transposed, for the back-transform
-                if (warp == wlast && tc == 0) {
-                    store_vec<TR>(S.hu[k & 1] + i0, vr);
-#pragma unroll
-                    for (int ii = 0; ii < TR; ++ii) S.A[yt_index<NMAX>(i0 + ii, k)] = vr[ii];
-                    if (lane == 0) {
-                        S.e[k] = beta;
-                        S.tau[k] = tau;
-                    }
-                }
-                // column sums of the updated tile with v_k
-                float s[TC];
-#pragma unroll
-                for (int jj = 0; jj < TC; ++jj) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int ii = 0; ii < TR; ++ii) acc = fmaf(a[ii][jj], vr[ii], acc);
-                    s[jj] = acc;
-                }
-                // sum over the row lanes: halving exchanges leave the lowest LOG_TC row-lane bits
-                // holding one column each, plain butterflies finish the sum
-                int cb = 0;
-#pragma unroll
-                for (int l = 0; l < LOG_TC; ++l) {
-                    const int h = TC >> (l + 1);
-                    const int o = NTC << l;
-                    const bool up = (lane & o) != 0;
-#pragma unroll
-                    for (int t = 0; t < h; ++t) {
-                        const float send = up ? s[t] : s[t + h];
-                        const float keep = up ? s[t + h] : s[t];
-                        s[t] = keep + __shfl_xor_sync(kFull, send, o);
-                    }
-                    if (up) cb += h;
-                }
-#pragma unroll
-                for (int o = NTC << LOG_TC; o < 32; o <<= 1) s[0] += __shfl_xor_sync(kFull, s[0], o);
-                float* Pw = S.hp[k & 1];
-                if ((lane >> (LOG_NTC + LOG_TC)) == 0) Pw[j0 + cb] = tau * s[0];
-            }
-            tau_prev = tau;
-            team_sync<NT>(bar_id);
-        }
+        a1_run<NMAX, G, TR>(S, a, 0, n, tau_prev, tid, bar_id);
         // reflector columns n - 2 .. of the last back-transform block are zero
         for (int idx = tid; idx < NMAX * kBT; idx += NT) {
             const int i = idx / kBT, kk = n - 2 + idx % kBT;
             if (n >= 3 && kk < NMAX) S.A[yt_index<NMAX>(i, kk)] = 0.f;
-        }
-        // the trailing 2 x 2 block after the last update (the whole matrix when n <= 2)
-        const int kf = n - 2;
-        if (n >= 2 && warp * WC + WC > kf && warp <= wlast) {
-            const float* Pr = S.hp[(kf + 1) & 1];
-            const float* Ur = S.hu[(kf + 1) & 1];
-            float dot = 0.f;
-#pragma unroll
-            for (int ii = 0; ii < TR; ++ii) dot = fmaf(Pr[i0 + ii], Ur[i0 + ii], dot);
-            const float c = 0.5f * tau_prev * row_lane_sum<NTC>(dot);
-#pragma unroll
-            for (int ii = 0; ii < TR; ++ii)
-#pragma unroll
-                for (int jj = 0; jj < TC; ++jj) {
-                    const int i = i0 + ii, j = j0 + jj;
-                    if (i >= kf && j >= kf && i < n && j < n && j <= i) {
-                        const float ui = Ur[i], uj = Ur[j];
-                        const float wi = fmaf(-c, ui, Pr[i]), wj = fmaf(-c, uj, Pr[j]);
-                        const float x = fmaf(-ui, wj, fmaf(-wi, uj, a[ii][jj]));
-                        if (i == j) S.d[i] = x;
-                        else S.e[kf] = x;
-                    }
-                }
-        } else if (n == 1 && tid == 0) {
-            S.d[0] = a[0][0];
         }
         team_sync<NT>(bar_id);
     }
