@@ -295,11 +295,12 @@ def run_ours(args, rank, world, local):
     order = sorted(SIZES, reverse=True)  # the longest launch first
 
     # every size with the leaf size the autotuner's table gives it (the same per-n choice the ragged
-    # kernel makes) and the uniform kernel's automatic team shape
+    # kernel makes) and the team shape for sizes launched side by side (the uniform kernel's automatic
+    # shape, except 64-thread teams for n = 17..32: the choice of bed_eigh_many_f32_pinned for a mix)
     from paper_2604_27325_gb300 import autotune
 
     tuning = autotune.load()
-    tuned = {n: autotune.uniform_params(n, tuning) for n in SIZES}
+    tuned = {n: autotune.uniform_params(n, tuning, concurrent=True) for n in SIZES}
 
     def launch(n, s=None, params=None):
         st = B.bed_eigh_f32(Ad[n].data_ptr(), Wd[n].data_ptr(), Vd[n].data_ptr(), Id[n].data_ptr(), BATCH, n,
@@ -482,7 +483,7 @@ def run_ours(args, rank, world, local):
             a, w, v = groups[n]
             g_side[n].wait_event(fork)
             st = B.bed_eigh_f32(a.data_ptr(), w.data_ptr(), v.data_ptr(), None, a.shape[0], n,
-                                autotune.uniform_params(n, tuning), g_side[n].cuda_stream)
+                                autotune.uniform_params(n, tuning, concurrent=True), g_side[n].cuda_stream)
             if st != B.BED_OK:
                 raise B.BedError(B.bed_status_string(st))
             j = torch.cuda.Event()
@@ -664,9 +665,10 @@ def run_ours(args, rank, world, local):
     best_uniform = max(value, uniform_via_ragged)
     launch = ("one ragged persistent launch (plus its one-block ordering pass) per step, CUDA-graph replay"
               if uniform_via_ragged > value else
-              "one launch per n (leaf size from the autotuner table, automatic team shape), each on its own "
-              "stream forked from and joined to the timing stream, the step captured once as a CUDA graph and "
-              "replayed")
+              "one launch per n (leaf size from the autotuner table; threads per matrix "
+              + ", ".join(f"{n}: {B.team_threads(n, tuned[n])}" for n in SIZES)
+              + "), each on its own stream forked from and joined to the timing stream, the step captured once "
+              "as a CUDA graph and replayed")
     line = {
         "metric": METRIC, "value": best_uniform, "unit": "matrices/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

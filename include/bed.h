@@ -175,6 +175,10 @@ bed_status bed_eigh_f32_pinned(const float* A_host, float* W_host, float* V_host
  *                    for all of them (through two events the library keeps per calling thread)
  *   side, nside      streams the launches run on, largest n first, batch j of that order on
  *                    side[j % nside], so that batches of different n run side by side
+ *   p                NULL or parameters for every batch. When more than one stream is used and
+ *                    threads_per_matrix is 0 (automatic), batches of 17..32 rows run 64-thread teams
+ *                    rather than 128: half the registers per matrix, so that more of them fit beside the
+ *                    larger sizes' blocks (alone, such a batch is faster with 128 threads)
  * Every argument of every batch is checked before anything is enqueued (BED_ERR_UNSUPPORTED_N,
  * BED_ERR_INVALID_ARG); after a CUDA error (BED_ERR_CUDA) earlier launches of the call may stay
  * enqueued, still joined to `origin`.

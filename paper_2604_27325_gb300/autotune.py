@@ -91,13 +91,17 @@ def load(path: str | None = None) -> B.bed_ragged_tuning:
 TEAM_THREADS = {0: 256, 1: 128, 2: 64, 3: 32, 4: 192}
 
 
-def uniform_params(n: int, tuning: B.bed_ragged_tuning | None = None, same_team: bool = False) -> B.bed_params:
+def uniform_params(n: int, tuning: B.bed_ragged_tuning | None = None, same_team: bool = False,
+                   concurrent: bool = False) -> B.bed_params:
     """Parameters of a uniform-size launch (bed_eigh_f32) with the leaf size the tuning table gives size n
     and the uniform kernel's automatic team shape; with ``same_team`` the team shape of the table too,
-    so that a uniform launch runs exactly (bitwise) what the ragged kernel would for n."""
+    so that a uniform launch runs exactly (bitwise) what the ragged kernel would for n. With
+    ``concurrent`` (launches of several sizes side by side) sizes 17..32 get 64-thread teams, the choice
+    bed_eigh_many_f32_pinned makes for such a mix: half the registers of the automatic 128-thread team,
+    so that more of them fit beside the larger sizes' blocks."""
     t = tuning if tuning is not None else load()
-    tpm = TEAM_THREADS[int(t.team[n])] if same_team else 0
-    return B.make_params(threads_per_matrix=tpm, leaf_size=int(t.leaf[n]))
+    p = B.make_params(threads_per_matrix=TEAM_THREADS[int(t.team[n])] if same_team else 0, leaf_size=int(t.leaf[n]))
+    return B.concurrent_params(p, n, 2) if concurrent else p
 
 
 if __name__ == "__main__":

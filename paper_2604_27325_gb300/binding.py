@@ -371,6 +371,28 @@ def make_params(**kw) -> bed_params:
     return p
 
 
+def concurrent_params(params: bed_params | None, n: int, count: int) -> bed_params | None:
+    """The parameters a batch of size n gets when ``count`` batches run side by side (the rule of
+    bed_eigh_many_f32_pinned): with the team shape left automatic and count > 1, sizes 17..32 run
+    64-thread teams, half the registers of the automatic 128-thread team, so that more of them fit beside
+    the larger sizes' blocks."""
+    if count > 1 and 16 < n <= 32 and (params is None or params.threads_per_matrix == 0):
+        q = bed_params.from_buffer_copy(params if params is not None else bed_default_params())
+        q.threads_per_matrix = 64
+        return q
+    return params
+
+
+def team_threads(n: int, params: bed_params | None = None) -> int:
+    """Threads per matrix of a uniform launch of size n with these parameters (the rule bed.h states for
+    threads_per_matrix: automatic 4 nmax threads, 128 for nmax = 64 without the tensor-core merges)."""
+    p = params if params is not None else bed_default_params()
+    if p.threads_per_matrix:
+        return int(p.threads_per_matrix)
+    nmax = next(m for m in (16, 32, 48, 64) if m >= n)
+    return 128 if (nmax == 64 and not p.merge_tensor_cores) else 4 * nmax
+
+
 def batched_eigh(A: torch.Tensor, params: bed_params | None = None, check: bool = False,
                  return_info: bool = False, counters: torch.Tensor | None = None):
     """Eigendecomposition of a batch of symmetric FP32 matrices ``A[..., n, n]`` (lower triangle read).
@@ -537,7 +559,8 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
     the CPU or all on one CUDA device.
 
     Each batch gets one launch on its own stream, forked from the current stream and joined back to it,
-    so that batches of different n run side by side on the GPU instead of one after another. CPU tensors
+    so that batches of different n run side by side on the GPU instead of one after another; with the
+    team shape left automatic, batches of 17..32 rows then run 64-thread teams (:func:`concurrent_params`). CPU tensors
     are solved in place in page-locked host memory (``bed_eigh_many_f32_pinned``: the kernels read the
     matrices and write the results across the host-device link, no device buffers, one call for all
     batches); with ``host_chunks > 0`` they go through ``bed_eigh_f32_host`` instead (copy in, solve and
@@ -558,6 +581,7 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
     cur = torch.cuda.current_stream(dev)
     if host and host_chunks <= 0:
         return _many_pinned(mats, params, check, return_info, dev, cur)
+    live = sum(1 for M in mats if M.numel() > 0)  # batches that launch (the count the team rule sees)
     fork = torch.cuda.Event()
     fork.record(cur)
     # largest n first: its launch is the longest and should start first
@@ -585,7 +609,8 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
             for t in (Ad, Wd, Vd, Id):
                 t.record_stream(s1)
             keep.append((Ah, Ad, Wd, Vd, Id))
-            _check(bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n, params,
+            _check(bed_eigh_f32_host(Ah.data_ptr(), Wh.data_ptr(), Vh.data_ptr(), Ih.data_ptr(), b, n,
+                                     concurrent_params(params, n, live),
                                      Ad.data_ptr(), Wd.data_ptr(), Vd.data_ptr(), Id.data_ptr(), host_chunks,
                                      s0.cuda_stream, s1.cuda_stream))
             for s in (s0, s1):
@@ -596,7 +621,7 @@ def batched_eigh_many(mats, params: bed_params | None = None, check: bool = Fals
             s = side[k]
             s.wait_event(fork)
             with torch.cuda.stream(s):
-                outs[i] = _eigh_enqueue(mats[i], params, None)
+                outs[i] = _eigh_enqueue(mats[i], concurrent_params(params, mats[i].shape[-1], live), None)
             join = torch.cuda.Event()
             join.record(s)
             cur.wait_event(join)

@@ -481,11 +481,17 @@ bed_status bed_eigh_many_f32_pinned(int count, const int* ns, const int64_t* bat
         e = cudaStreamWaitEvent(side[s], ev->fork, 0);
         if (e != cudaSuccess) return bed::cuda_fail(e);
     }
+    // With the team shape left automatic and several batches side by side, sizes 17..32 run 64-thread
+    // teams (two lanes per row): half the registers of the 128-thread team, so that more of them share
+    // the SMs with the larger sizes' blocks (a lone launch of such a batch is faster with 128 threads)
+    const bool concurrent = used > 1 && prm.threads_per_matrix == 0;
     bed_status st = BED_OK;
     for (size_t j = 0; j < order.size() && st == BED_OK; ++j) {
         const int k = order[j];
-        st = bed::eigh_common(dp[k].A, dp[k].W, dp[k].V, dp[k].info, batches[k], ns[k], p, nullptr, side[j % used],
-                              true);
+        bed_params pk = prm;
+        if (concurrent && ns[k] > 16 && ns[k] <= 32) pk.threads_per_matrix = 64;
+        st = bed::eigh_common(dp[k].A, dp[k].W, dp[k].V, dp[k].info, batches[k], ns[k], &pk, nullptr,
+                              side[j % used], true);
     }
     // join even after a failed launch, so that `origin` still orders after whatever was enqueued
     for (int s = 0; s < used; ++s) {

@@ -64,8 +64,8 @@ struct Smem {
     float sgn[NMAX];
     float cinv[NMAX];  // merge: 1 / norm of each column of Q^ (P7), applied by P8
     float brho[NB], btol[NB], bsc[NB];  // per merge of a level: |beta|, tolerance, scale
-    int rank[NMAX];   // column c of the children -> its sorted position
-    int inv[NMAX];    // compacted index -> sorted position
+    int colof[NMAX];  // sorted position -> the column of the children it came from
+    int inv[NMAX];    // compacted index -> column of the children (the row of Q^ in M)
     float dorg[NMAX];  // root -> the (scaled) pole it is measured from, d_o
     int rotj[NMAX];   // sorted position -> rotation partner (-1: none)
     int defl[NMAX];
@@ -714,7 +714,7 @@ __device__ __forceinline__ void merge_product_fma(Smem<NMAX, G>& S, const Plan& 
         const float* qrow = S.Q + r0 * LD;
 #pragma unroll 2
         for (int c = c0; c < c1; ++c) {
-            const float* mrow = S.M + S.rank[c] * LD + q0;
+            const float* mrow = S.M + c * LD + q0;
             float mv[PC];
 #pragma unroll
             for (int j = 0; j < PC; ++j) mv[j] = mrow[j];
@@ -782,8 +782,8 @@ __device__ __forceinline__ void merge_product_tc(Smem<NMAX, G>& S, const Plan& p
             const float x1 = (rb < rend && ka < c1) ? S.Q[rb * LD + ka] : 0.f;
             const float x2 = (ra < rend && kb < c1) ? S.Q[ra * LD + kb] : 0.f;
             const float x3 = (rb < rend && kb < c1) ? S.Q[rb * LD + kb] : 0.f;
-            const float y0 = (ka < c1 && nq < qend) ? S.M[S.rank[ka] * LD + nq] : 0.f;
-            const float y1 = (kb < c1 && nq < qend) ? S.M[S.rank[kb] * LD + nq] : 0.f;
+            const float y0 = (ka < c1 && nq < qend) ? S.M[ka * LD + nq] : 0.f;
+            const float y1 = (kb < c1 && nq < qend) ? S.M[kb * LD + nq] : 0.f;
             uint32_t ah[4], al[4], bh[2], bl[2];
             split_tf32(x0, ah[0], al[0]);
             split_tf32(x1, ah[1], al[1]);
@@ -1306,7 +1306,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                 const float bscale = fmaxf(dmax, rho * nz2);
                 const float nz = sqrt_approx(nz2);
                 const float tol = kp.defl_c * kU * bscale;
-                S.rank[c] = lo + p;
+                S.colof[lo + p] = c;
                 S.ds[lo + p] = S.lam[c];
                 S.zs[lo + p] = zc;
                 S.defl[lo + p] = (rho * fabsf(zc) * nz <= tol);  // deflation of a negligible coupling
@@ -1340,7 +1340,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             K = gsumi<G>(K);
             if (act && sub == 0) {
                 const int q = S.defl[t] ? (K + (t - lo - nb)) : nb;
-                S.inv[lo + q] = t;
+                S.inv[lo + q] = S.colof[t];
                 S.cdz[lo + q] = make_float2(S.ds[t] * S.bsc[lb], S.zs[t] * S.zs[t]);
                 S.cz[lo + q] = S.zs[t];
                 if (t == lo) S.bK[lb] = K;
@@ -1471,7 +1471,7 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
             if (own && sub == 0) S.zh[lo + i] = copysignf(sqrt_approx(fmaxf(prod, 0.f)), S.cz[lo + i]);
         }
         team_sync<NT>(bar_id);
-        // P7: eigenvectors of the merge (Eq. (24)) in sorted-pole rows, rotations undone
+        // P7: eigenvectors of the merge (Eq. (24)), row of sorted pole p at row colof[p] of M, rotations undone
         {
             int K = 0;
             if (act) K = S.bK[lb];
@@ -1504,15 +1504,17 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
                     const int j = S.rotj[p];
                     if (j >= 0) {
                         const float cc = S.rc[p], ss = S.rs[p];
-                        const float yp = S.M[p * LD + cq], yj = S.M[j * LD + cq];
-                        S.M[p * LD + cq] = fmaf(cc, yp, ss * yj);
-                        S.M[j * LD + cq] = fmaf(-ss, yp, cc * yj);
+                        const int rp = S.colof[p] * LD + cq, rj = S.colof[j] * LD + cq;
+                        const float yp = S.M[rp], yj = S.M[rj];
+                        S.M[rp] = fmaf(cc, yp, ss * yj);
+                        S.M[rj] = fmaf(-ss, yp, cc * yj);
                     }
                 }
             }
         }
         team_sync<NT>(bar_id);
-        // P8: Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)); rows of Q^ are gathered through the pole order
+        // P8: Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)); P7 stored row c of Q^ (the sorted pole that column c of
+        // the children became) at row c of M, so that the product reads M in the children's column order
         if constexpr (TC) {
             constexpr int TPW = (32 / NW < 2) ? 2 : ((32 / NW > 8) ? 8 : 32 / NW);  // tiles per warp
             if (tc_level_tiles(plan, L) <= TPW * NW)

@@ -178,3 +178,18 @@ def test_async_api_has_no_cpu_path():
     with pytest.raises(B.BedError):
         B.batched_eigh_many([torch.eye(4).unsqueeze(0)])
 
+
+
+def test_team_shape_rule_and_concurrent_params():
+    """The threads-per-matrix rule of bed.h, and the 64-thread teams for n = 17..32 in a concurrent mix."""
+    from paper_2604_27325_gb300 import autotune
+
+    assert [B.team_threads(n) for n in (1, 16, 17, 32, 33, 48, 49, 64)] == [64, 64, 128, 128, 192, 192, 128, 128]
+    assert B.team_threads(64, B.make_params(merge_tensor_cores=1)) == 256
+    assert B.team_threads(20, B.make_params(threads_per_matrix=64)) == 64
+    t = B.bed_ragged_default_tuning()
+    for n in range(1, 65):
+        p = autotune.uniform_params(n, t, concurrent=True)
+        assert p.threads_per_matrix == (64 if 16 < n <= 32 else 0)
+        assert p.leaf_size == t.leaf[n]
+        assert autotune.uniform_params(n, t).threads_per_matrix == 0

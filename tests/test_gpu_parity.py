@@ -210,14 +210,17 @@ def test_thread_count_rejects_shapes_below_n():
 
 @pytest.mark.parametrize("where", ["host", "device"])
 def test_many_batches_on_streams_match_single_calls(where):
-    """batched_eigh_many runs each batch on its own stream; results are those of one call per batch."""
+    """batched_eigh_many runs each batch on its own stream; results are those of one call per batch with
+    the parameters a batch gets beside others (64-thread teams for 17..32 rows)."""
     mats = [torch.from_numpy(wl.covariance(40, n, seed=60 + n)) for n in (64, 17, 48, 5, 32)]
     if where == "device":
         mats = [M.cuda() for M in mats]
     many = B.batched_eigh_many(mats, return_info=True)
     torch.cuda.synchronize()
     for M, (W, V, info) in zip(mats, many):
-        W1, V1, info1 = B.batched_eigh(M, return_info=True)
+        p1 = B.concurrent_params(None, M.shape[-1], len(mats))
+        assert (p1 is not None) == (16 < M.shape[-1] <= 32)
+        W1, V1, info1 = B.batched_eigh(M, params=p1, return_info=True)
         torch.cuda.synchronize()
         assert W.is_cuda == (where == "device")
         assert torch.equal(W.cpu(), W1.cpu()) and torch.equal(V.cpu(), V1.cpu())
@@ -348,10 +351,11 @@ def test_many_pinned_entry_point():
     assert B.bed_eigh_many_f32_pinned(ns, bs, *args([t.data_ptr() for t in W]), None, cur.cuda_stream,
                                       [s.cuda_stream for s in side]) == B.BED_OK
     cur.synchronize()
+    live = sum(1 for b in bs if b)  # batches that launch, side by side on the two streams
     for k, (n, b) in enumerate(zip(ns, bs)):
         if b == 0:
             continue
-        Wg, Vg, ig = run_gpu(A[k].numpy())
+        Wg, Vg, ig = run_gpu(A[k].numpy(), B.concurrent_params(None, n, live))
         assert np.array_equal(W[k].numpy(), Wg) and np.array_equal(V[k].numpy(), Vg)
         assert np.array_equal(I[k].numpy(), ig)
     assert B.bed_eigh_many_f32_pinned([], [], [], [], [], None, None, cur.cuda_stream, []) == B.BED_OK
@@ -376,7 +380,8 @@ def test_many_async_in_flight_matches_synchronous():
 def test_uniform_workload_end_to_end_path_at_full_size():
     """The benchmark's end-to-end configuration: the uniform workload (512 matrices at each of
     n = 16, 32, 48, 64) from page-locked host memory through batched_eigh_many_async with two calls in
-    flight; every result equals the device path bitwise, and a sample of each size matches the oracle."""
+    flight; every result equals the device path (with the parameters a batch gets beside the others)
+    bitwise, and a sample of each size matches the oracle."""
     sizes = (16, 32, 48, 64)
     host = [torch.from_numpy(wl.covariance(512, n)).pin_memory() for n in sizes]
     p1 = B.batched_eigh_many_async(host)
@@ -385,7 +390,7 @@ def test_uniform_workload_end_to_end_path_at_full_size():
     r2 = p2.wait(return_info=True)
     rng = np.random.default_rng(5)
     for n, A, (W, V, info), (W2, V2, info2) in zip(sizes, host, r1, r2):
-        Wd, Vd, infod = run_gpu(A.numpy())
+        Wd, Vd, infod = run_gpu(A.numpy(), B.concurrent_params(None, n, len(sizes)))
         assert np.array_equal(W.numpy(), Wd) and np.array_equal(V.numpy(), Vd) and np.array_equal(info.numpy(), infod)
         assert torch.equal(W, W2) and torch.equal(V, V2)
         idx = np.sort(rng.choice(512, 24, replace=False))
