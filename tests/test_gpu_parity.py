@@ -188,6 +188,19 @@ def test_large_batch_sampled():
     assert_parity(A[idx], W[idx], V[idx], info[idx], Wo, Vo, "sampled large batch")
 
 
+@pytest.mark.parametrize("nmax,tpm", [(16, 32), (32, 64), (48, 96), (64, 256)])
+def test_every_n_on_the_other_team_shape(nmax, tpm):
+    """Every n of a size class on the team shape that the automatic choice does not give it alone (two
+    lanes per row for 16, 32 and 48 rows -- the 64-thread teams are what sizes 17..32 run beside other
+    sizes -- and four lanes per row for 64), covariances and gapped known spectra, against the oracle."""
+    p = B.make_params(threads_per_matrix=tpm)
+    for n in range(nmax - 15, nmax + 1):
+        A = np.concatenate([wl.covariance(6, n, seed=9600 + n), wl.known_spectrum(4, n, seed=9700 + n)[0]])
+        W, V, info = run_gpu(A, p)
+        Wo, Vo = run_oracle(A)
+        assert_parity(A, W, V, info, Wo, Vo, f"n={n} threads={tpm}")
+
+
 @pytest.mark.parametrize("tpm", [96, 192, 128, 256])
 def test_thread_count_selects_team_shape_n40(tpm):
     """n = 40 runs on the 48-row team (96 or 192 threads) or, when asked, the 64-row team (128, 256):
