@@ -4,7 +4,8 @@
 //   a0  stage A[b] into shared memory (TMA bulk copy + mbarrier, or coalesced loads), read the lower
 //       triangle, check finiteness, scale by a power of two
 //   a1  Householder tridiagonalization: A in column-owned register tiles, p = tau A v from the
-//       column sums of each warp's block (A is symmetric), one block barrier per reflector
+//       column sums of each warp's block (A is symmetric), one block barrier per reflector; the
+//       steps run in phases of 16 that drop the rows below the phase's first step
 //   a2  tear the tridiagonal along the static divide tree (Sec. 2.1, Eq. (2)-(3))
 //   a3  leaves (Sec. 2.2): 1x1; 2x2 by one Jacobi rotation; 3 to 8 rows by implicit QL with
 //       Wilkinson shifts
@@ -15,7 +16,7 @@
 //   a6  Gu-Eisenstat z-hat (Eq. (25)) and eigenvectors (Eq. (24)), normalized by a7
 //   a7  merge GEMM Q <- blkdiag(Q1, Q2) Q^ (Eq. (4)) in register tiles of 4 rows x 16/G columns
 //   a8  back-transform through the Householder reflectors, 8 at a time as I - Y T Y^T, with each
-//       column of Q held in the registers of its G lanes
+//       column of Q held in the registers of its G lanes and the rows above each block skipped
 //   a9  ascending order, sign convention, store
 // Thread layouts (NT = NMAX * G threads): "position" pos = tid / G, sub = tid % G: G consecutive
 // lanes share one row / column and combine their partial results with shuffles inside the group;
