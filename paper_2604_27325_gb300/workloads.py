@@ -96,6 +96,18 @@ def differentiation(batch: int = 1024, n: int = 32, seed: int = SEED_DIFF, min_g
     return out, w, G
 
 
+def graded(batch: int, n: int, seed: int = 9, decades: float = 6.0):
+    """Symmetric N(0,1) matrices scaled two-sidedly by a geometric grading g_i = 10^(-t i/(n-1)),
+    t ~ U[0, decades] per batch entry: entries (and eigenvalues) spread over up to `decades` orders of
+    magnitude, the large ones in the leading rows. FP32 [batch, n, n]."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((batch, n, n))
+    S = (X + np.swapaxes(X, 1, 2)) / 2
+    t = rng.uniform(0.0, decades, batch)
+    g = 10.0 ** (-t[:, None] * np.linspace(0.0, 1.0, n)[None, :])
+    return _sym32(S * g[:, :, None] * g[:, None, :])
+
+
 def special_cases(n: int, seed: int = 7):
     """Degenerate inputs that force every branch: zero, identity, diagonal, repeated eigenvalues,
     a rank-one matrix, a block-diagonal matrix (exact zero couplings), a tridiagonal Toeplitz matrix.

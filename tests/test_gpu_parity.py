@@ -188,6 +188,23 @@ def test_large_batch_sampled():
     assert_parity(A[idx], W[idx], V[idx], info[idx], Wo, Vo, "sampled large batch")
 
 
+@pytest.mark.parametrize("seed", [1, 2])
+def test_every_n_random_families_both_team_shapes(seed):
+    """Every n, three input families (covariances, gapped known spectra, graded matrices whose entries
+    span up to six orders of magnitude), on the automatic team shape and on the other one of its size
+    class, against the oracle."""
+    for n in range(1, 65):
+        nmax = next(m for m in (16, 32, 48, 64) if m >= n)
+        other = 256 if nmax == 64 else 2 * nmax
+        A = np.concatenate([wl.covariance(4, n, seed=10000 * seed + n),
+                            wl.known_spectrum(4, n, seed=20000 * seed + n)[0],
+                            wl.graded(4, n, seed=30000 * seed + n)])
+        Wo, Vo = run_oracle(A)
+        for tpm in (0, other):
+            W, V, info = run_gpu(A, B.make_params(threads_per_matrix=tpm))
+            assert_parity(A, W, V, info, Wo, Vo, f"seed={seed} n={n} threads={tpm}")
+
+
 @pytest.mark.parametrize("nmax,tpm", [(16, 32), (32, 64), (48, 96), (64, 256)])
 def test_every_n_on_the_other_team_shape(nmax, tpm):
     """Every n of a size class on the team shape that the automatic choice does not give it alone (two

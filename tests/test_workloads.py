@@ -37,3 +37,14 @@ def test_special_cases_are_symmetric():
     for n in (1, 2, 5, 16):
         for name, M in wl.special_cases(n).items():
             assert M.shape == (n, n) and np.array_equal(M, M.T), name
+
+
+def test_graded_matrices_are_symmetric_seeded_and_graded():
+    A = wl.graded(16, 12, seed=5)
+    assert A.shape == (16, 12, 12) and A.dtype == np.float32
+    assert np.array_equal(A, np.swapaxes(A, 1, 2))
+    assert np.array_equal(A, wl.graded(16, 12, seed=5)) and not np.array_equal(A, wl.graded(16, 12, seed=6))
+    # entries spread over several orders of magnitude (the grading reaches up to 10^-6 per side)
+    ratios = np.abs(A).max(axis=(1, 2)) / np.abs(A).min(axis=(1, 2))
+    assert ratios.max() > 1e4
+    assert wl.graded(2, 1).shape == (2, 1, 1)
