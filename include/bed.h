@@ -91,6 +91,10 @@ typedef struct {
                                 in shared memory, 0..60,000,000 (default 2,000,000); a matrix whose copy has
                                 not landed by then gets BED_INFO_TIMEOUT. 0 gives up without waiting, which
                                 exercises that path deterministically (the copy is still drained). */
+    int matrices_per_cta;    /* uniform launches (bed_eigh_f32*): 0 (default) one thread block per matrix; k
+                                in 1..2^20: ceil(batch / k) blocks, block i solving matrices i, i + blocks,
+                                ... in turn (about k each) in its shared memory. Results are bitwise the same
+                                whatever k; the ragged kernel and the server hand out their own units. */
 } bed_params;
 
 /* Fills *p with the defaults listed above. */

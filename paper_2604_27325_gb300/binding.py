@@ -42,6 +42,7 @@ class bed_params(C.Structure):
         ("retire_by_vote", C.c_int),
         ("merge_tensor_cores", C.c_int),
         ("stage_wait_us", C.c_int),
+        ("matrices_per_cta", C.c_int),
     ]
 
 

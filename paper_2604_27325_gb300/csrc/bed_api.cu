@@ -114,14 +114,14 @@ const Plan* cached_plan(int n, int leaf_size)
 }
 
 cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int32_t* info,
-                        int64_t batch, const Plan& P, const KParams& kp, bed_counters* counters,
-                        bool bulk, cudaStream_t stream)
+                        int64_t batch, int64_t blocks, const Plan& P, const KParams& kp,
+                        bed_counters* counters, bool bulk, cudaStream_t stream)
 {
-#define BED_CASE(NM, GG)                                                                             \
-    if (nmax == NM && g == GG) {                                                                     \
-        if (GG == 4 && kp.merge_tc)                                                                  \
-            return launch_eigh_t<NM, 4, true>(A, W, V, info, batch, P, kp, counters, bulk, stream);  \
-        return launch_eigh_t<NM, GG>(A, W, V, info, batch, P, kp, counters, bulk, stream);           \
+#define BED_CASE(NM, GG)                                                                                   \
+    if (nmax == NM && g == GG) {                                                                           \
+        if (GG == 4 && kp.merge_tc)                                                                        \
+            return launch_eigh_t<NM, 4, true>(A, W, V, info, batch, blocks, P, kp, counters, bulk, stream); \
+        return launch_eigh_t<NM, GG>(A, W, V, info, batch, blocks, P, kp, counters, bulk, stream);         \
     }
     BED_CASE(16, 2)
     BED_CASE(16, 4)
@@ -150,6 +150,7 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
     if (prm->retire_by_vote != 0 && prm->retire_by_vote != 1) return false;
     if (prm->merge_tensor_cores != 0 && prm->merge_tensor_cores != 1) return false;
     if (prm->stage_wait_us < 0 || prm->stage_wait_us > 60000000) return false;
+    if (prm->matrices_per_cta < 0 || prm->matrices_per_cta > (1 << 20)) return false;
     kp->k_ms = prm->k_multisection;
     kp->max_sec = prm->max_section_iters;
     kp->max_halley = prm->max_halley_iters;
@@ -217,7 +218,9 @@ bed_status eigh_common(const float* A, float* W, float* V, int32_t* info, int64_
     // every matrix: A 16-byte aligned and n even.
     // Matrices in mapped host memory are read with plain loads.
     const bool bulk = !host_mapped && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && (n % 2 == 0);
-    const cudaError_t e = launch_eigh(nmax, g, A, W, V, info, batch, *P, kp, counters, bulk, stream);
+    const int64_t mpc = prm.matrices_per_cta;
+    const int64_t blocks = mpc > 0 ? (batch + mpc - 1) / mpc : batch;
+    const cudaError_t e = launch_eigh(nmax, g, A, W, V, info, batch, blocks, *P, kp, counters, bulk, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     return BED_OK;
 }
@@ -298,6 +301,7 @@ void bed_default_params(bed_params* p)
     p->retire_by_vote = 1;
     p->merge_tensor_cores = 0;
     p->stage_wait_us = 2000000;
+    p->matrices_per_cta = 0;
 }
 
 bed_status bed_eigh_f32(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,

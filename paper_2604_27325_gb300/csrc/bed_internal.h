@@ -47,11 +47,12 @@ bool build_plan(int n, int leaf_size, Plan* P);
 // Leaf size used for n when bed_params.leaf_size is 0 (automatic).
 int auto_leaf(int n);
 
-// One kernel launch over the whole batch. nmax in {16, 32, 64}, g in {2, 4} (threads = nmax * g).
+// One kernel launch over the whole batch. nmax in {16, 32, 64}, g in {2, 4} (threads = nmax * g);
+// `blocks` thread blocks (>= 1), block i solving matrices i, i + blocks, ...
 // bulk: stage each matrix with a TMA bulk copy (requires 16-byte aligned A and even n).
 cudaError_t launch_eigh(int nmax, int g, const float* A, float* W, float* V, int32_t* info,
-                        int64_t batch, const Plan& P, const KParams& kp, bed_counters* counters,
-                        bool bulk, cudaStream_t stream);
+                        int64_t batch, int64_t blocks, const Plan& P, const KParams& kp,
+                        bed_counters* counters, bool bulk, cudaStream_t stream);
 
 cudaError_t launch_ragged(const float* A, const int64_t* offsets, const int32_t* ns, int64_t count, float* W,
                           const int64_t* w_offsets, float* V, int32_t* info, const bed_ragged_tuning& tuning,
@@ -94,7 +95,7 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp);
 
 // TC: the merge products on the tensor cores (split-3xTF32), instantiated for G = 4 teams only.
 template <int NMAX, int G, bool TC = false>
-cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int64_t batch,
+cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int64_t batch, int64_t blocks,
                           const Plan& P, const KParams& kp, bed_counters* counters, bool bulk,
                           cudaStream_t stream);
 

@@ -1821,7 +1821,7 @@ __global__ void __launch_bounds__(NMAX * G, eigh_min_blocks<NMAX, G>())
 }
 
 template <int NMAX, int G, bool TC>
-cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int64_t batch,
+cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int64_t batch, int64_t blocks,
                           const Plan& P, const KParams& kp, bed_counters* counters, bool bulk,
                           cudaStream_t stream)
 {
@@ -1843,7 +1843,7 @@ cudaError_t launch_eigh_t(const float* A, float* W, float* V, int32_t* info, int
         configured.fetch_or(bit, std::memory_order_release);
     }
     const int64_t max_grid = 2147483647LL;
-    const unsigned grid = static_cast<unsigned>(batch < max_grid ? batch : max_grid);
+    const unsigned grid = static_cast<unsigned>(blocks < max_grid ? blocks : max_grid);
     kern<<<grid, NMAX * G, smem, stream>>>(A, W, V, info, batch, P, kp, counters, bulk ? 1 : 0);
     return cudaGetLastError();
 }

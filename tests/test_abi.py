@@ -37,7 +37,7 @@ def test_constants_and_strings():
     assert C.sizeof(B.bed_counters) == 32
     p = B.bed_default_params()
     assert (p.leaf_size, p.k_multisection, p.retire_by_vote, p.threads_per_matrix) == (0, 4, 1, 0)
-    assert p.merge_tensor_cores == 0
+    assert p.merge_tensor_cores == 0 and p.matrices_per_cta == 0
     assert p.section_rel_eps == 2.0**-1
 
 
@@ -69,7 +69,8 @@ def test_empty_batch_is_ok_without_launch():
     [("leaf_size", 9), ("leaf_size", -1), ("k_multisection", 1), ("max_halley_iters", 0),
      ("max_section_iters", -1), ("section_rel_eps", 0.0), ("section_rel_eps", 1.0), ("stop_c", 0.5),
      ("deflation_tol_scale", 0.0), ("retire_by_vote", 2), ("threads_per_matrix", 100),
-     ("merge_tensor_cores", 2), ("merge_tensor_cores", -1)],
+     ("merge_tensor_cores", 2), ("merge_tensor_cores", -1), ("matrices_per_cta", -1),
+     ("matrices_per_cta", (1 << 20) + 1)],
 )
 def test_bad_params(field, value):
     p = B.make_params(**{field: value})

@@ -188,6 +188,20 @@ def test_large_batch_sampled():
     assert_parity(A[idx], W[idx], V[idx], info[idx], Wo, Vo, "sampled large batch")
 
 
+@pytest.mark.parametrize("n", [7, 20, 48, 64])
+def test_matrices_per_block_gives_the_same_results(n):
+    """matrices_per_cta = k: ceil(batch / k) blocks each solving several matrices in turn (the staging
+    copy and its mbarrier reused from one matrix to the next) give bitwise the one-block-per-matrix
+    results, on the bulk-copy path (even n) and the plain-load path (odd n)."""
+    A = np.concatenate([wl.covariance(45, n, seed=1200 + n), wl.known_spectrum(12, n, seed=1300 + n)[0]])
+    W0, V0, i0 = run_gpu(A)
+    for k in (1, 3, 8, 1000):
+        W, V, info = run_gpu(A, B.make_params(matrices_per_cta=k))
+        assert np.array_equal(W, W0) and np.array_equal(V, V0) and np.array_equal(info, i0), k
+    Wo, Vo = run_oracle(A)
+    assert_parity(A, W0, V0, i0, Wo, Vo, f"n={n}")
+
+
 @pytest.mark.parametrize("seed", [1, 2])
 def test_every_n_random_families_both_team_shapes(seed):
     """Every n, three input families (covariances, gapped known spectra, graded matrices whose entries
