@@ -1155,21 +1155,21 @@ __device__ __forceinline__ bool solve_matrix(Smem<NMAX, G>& S, const Plan& plan,
         constexpr int WC = NMAX / NW;             // columns per warp
         constexpr int NTC = a1_col_lanes<NMAX, G>();  // lanes along the columns
         constexpr int NTR = 32 / NTC;             // lanes along the rows
-        constexpr int TC = WC / NTC;              // tile columns per lane
+        constexpr int TCOL = WC / NTC;            // tile columns per lane
         constexpr int TR = NMAX / NTR;            // tile rows per lane
-        constexpr int LOG_TC = ilog2(TC);
+        constexpr int LOG_TCOL = ilog2(TCOL);
         constexpr int LOG_NTC = ilog2(NTC);
-        static_assert(WC * NW == NMAX && TR * NTR == NMAX && TC * NTC == WC && (1 << LOG_TC) == TC &&
-                          (1 << LOG_NTC) == NTC && NTR == 16 && TC == a1_tile_cols<NMAX, G>(),
+        static_assert(WC * NW == NMAX && TR * NTR == NMAX && TCOL * NTC == WC && (1 << LOG_TCOL) == TCOL &&
+                          (1 << LOG_NTC) == NTC && NTR == 16 && TCOL == a1_tile_cols<NMAX, G>(),
                       "tile shape");
         const int tr = lane / NTC, tc = lane % NTC;
-        const int i0 = tr * TR, j0 = warp * WC + tc * TC;
-        float a[TR][TC];
+        const int i0 = tr * TR, j0 = warp * WC + tc * TCOL;
+        float a[TR][TCOL];
         // the tile comes straight from the staged input (row-major n x n, lower triangle read), scaled
 #pragma unroll
         for (int ii = 0; ii < TR; ++ii)
 #pragma unroll
-            for (int jj = 0; jj < TC; ++jj) {
+            for (int jj = 0; jj < TCOL; ++jj) {
                 const int i = i0 + ii, j = j0 + jj;
                 a[ii][jj] = (i < n && j < n) ? S.M[(j <= i) ? (i * n + j) : (j * n + i)] * scale : 0.f;
             }
