@@ -583,8 +583,9 @@ def run_ours(args, rank, world, local):
     serving = None
     if args.serving_seconds > 0:
         pool = serve.request_pool()
-        keep = ("p50_ms", "p99_ms", "mean_ms", "matrices_per_s", "requests", "offered_requests", "launches",
-                "requests_per_launch", "achieved_submit_rate", "peak_device_bytes")
+        keep = ("p50_ms", "p99_ms", "mean_ms", "max_ms", "matrices_per_s", "requests", "offered_requests", "launches",
+                "requests_per_launch", "achieved_submit_rate", "peak_device_bytes", "max_admit_wait_ms",
+                "max_enqueue_ms", "max_inflight_ms")
 
         def load(mode, rate, seconds):
             srv = serve.NativeServer(budget_bytes=4 << 30, tuning=tuning if mode == "batch" else None, mode=mode)

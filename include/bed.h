@@ -319,6 +319,10 @@ typedef struct {
     int64_t peak_device_bytes;            /* largest arena footprint admitted */
     double p50_s, p99_s, mean_s, max_s;   /* request latency: submit to results in host memory */
     double span_s;                        /* first submit to last completion */
+    /* where the slowest requests spent their time, each the largest since creation or the last reset:
+       submit to admission into a launch (waiting for a slot, or for memory that releases free), the
+       host enqueueing one launch, and a launch's enqueue to the completion thread seeing it done */
+    double max_admit_wait_s, max_enqueue_s, max_inflight_s;
 } bed_server_stats;
 
 void bed_server_default_config(bed_server_config* c);

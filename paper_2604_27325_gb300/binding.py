@@ -67,7 +67,8 @@ class bed_server_config(C.Structure):
 class bed_server_stats(C.Structure):
     _fields_ = [("requests", C.c_int64), ("matrices", C.c_int64), ("launches", C.c_int64),
                 ("peak_device_bytes", C.c_int64), ("p50_s", C.c_double), ("p99_s", C.c_double),
-                ("mean_s", C.c_double), ("max_s", C.c_double), ("span_s", C.c_double)]
+                ("mean_s", C.c_double), ("max_s", C.c_double), ("span_s", C.c_double),
+                ("max_admit_wait_s", C.c_double), ("max_enqueue_s", C.c_double), ("max_inflight_s", C.c_double)]
 
 
 EXPORTED = [

@@ -83,7 +83,7 @@ struct Request {
     int64_t id;
     const float* A;  // caller's host buffer
     int b, n;
-    double t_submit = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
     const float* A_in = nullptr;  // device-visible address of A when it is read in place (zero-copy)
     bool checked = false;         // A_in decided (at admission)
     int64_t a_off = -1;           // device input arena (staged input); the eigenvector arena uses it too
@@ -112,6 +112,7 @@ struct Slot {
 struct Launch {
     int slot;
     std::vector<Request*> reqs;
+    double t_start, t_enqueued;  // host clock when launch() began and when its work was enqueued
 };
 
 }  // namespace
@@ -140,6 +141,7 @@ struct bed_server {
     // statistics
     std::vector<double> lat;
     int64_t n_requests = 0, n_matrices = 0, n_launches = 0, peak_dev = 0;
+    double max_admit_wait = 0, max_enqueue = 0, max_inflight = 0;  // where a request's time went, at worst
     double t_first = 0, t_last = 0;
     std::thread sched, done;
     int64_t dev_bytes_in_use() const { return 4 * (2 * av->used() + w->used()); }
@@ -165,6 +167,7 @@ void release_device(bed_server* s, Request* r)
 
 void launch(bed_server* s, int si, std::vector<Request*>& batch)
 {
+    const double t_start = now_s();
     Slot& sl = s->slots[si];
     float* Ad = s->dev;
     float* Vd = s->dev + s->cap_av;
@@ -250,7 +253,9 @@ void launch(bed_server* s, int si, std::vector<Request*>& batch)
         s->cv.notify_all();
         return;
     }
-    s->inflight.push_back(Launch{si, batch});
+    const double t_enq = now_s();
+    s->max_enqueue = std::max(s->max_enqueue, t_enq - t_start);
+    s->inflight.push_back(Launch{si, batch, t_start, t_enq});
     ++s->n_launches;
     s->cv.notify_all();
 }
@@ -312,6 +317,7 @@ void scheduler(bed_server* s)
             r->w_off = wo;
             r->h_off = ho;
             r->state = 1;
+            r->t_admit = now_s();
             s->pending.pop_front();
             batch.push_back(r);
             count += r->b;
@@ -367,7 +373,9 @@ void completer(bed_server* s)
             auto it = std::find_if(s->inflight.begin(), s->inflight.end(),
                                    [&](const Launch& L) { return L.slot == f.first; });
             if (it == s->inflight.end()) continue;
+            s->max_inflight = std::max(s->max_inflight, t - it->t_enqueued);
             for (Request* r : it->reqs) {
+                s->max_admit_wait = std::max(s->max_admit_wait, r->t_admit - r->t_submit);
                 release_device(s, r);
                 r->state = 2;
                 r->t_done = t;
@@ -538,6 +546,9 @@ bed_status bed_server_get_stats(bed_server* s, bed_server_stats* out)
         out->mean_s = sum / v.size();
         out->max_s = v.back();
     }
+    out->max_admit_wait_s = s->max_admit_wait;
+    out->max_enqueue_s = s->max_enqueue;
+    out->max_inflight_s = s->max_inflight;
     return BED_OK;
 }
 
@@ -549,6 +560,7 @@ bed_status bed_server_reset_stats(bed_server* s)
     s->n_requests = s->n_matrices = s->n_launches = 0;
     s->peak_dev = s->dev_bytes_in_use();
     s->t_first = s->t_last = 0;
+    s->max_admit_wait = s->max_enqueue = s->max_inflight = 0;
     return BED_OK;
 }
 

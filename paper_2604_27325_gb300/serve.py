@@ -483,7 +483,9 @@ class NativeServer:
         out = {"requests": s.requests, "matrices": s.matrices, "launches": s.launches,
                "peak_device_bytes": s.peak_device_bytes}
         if s.requests:
-            out.update(p50_ms=s.p50_s * 1e3, p99_ms=s.p99_s * 1e3, mean_ms=s.mean_s * 1e3, max_ms=s.max_s * 1e3)
+            out.update(p50_ms=s.p50_s * 1e3, p99_ms=s.p99_s * 1e3, mean_ms=s.mean_s * 1e3, max_ms=s.max_s * 1e3,
+                       max_admit_wait_ms=s.max_admit_wait_s * 1e3, max_enqueue_ms=s.max_enqueue_s * 1e3,
+                       max_inflight_ms=s.max_inflight_s * 1e3)
         if s.span_s > 0:
             out["matrices_per_s"] = s.matrices / s.span_s
         return out

@@ -125,6 +125,10 @@ def test_native_short_poisson_run():
     out = serve.run_load_native(srv, rate=1000.0, seconds=1.0, seed=23)
     srv.close()
     assert out["requests"] == out["offered_requests"] and out["p99_ms"] > 0
+    # each part of a request's time is bounded by the slowest request's whole latency
+    for part in ("max_admit_wait_ms", "max_enqueue_ms", "max_inflight_ms"):
+        assert 0.0 <= out[part] <= out["max_ms"] + 1e-6, (part, out[part], out["max_ms"])
+    assert out["max_inflight_ms"] > 0
 
 
 def test_native_server_zero_copy_equals_staged_and_unpinned_inputs_are_staged():
