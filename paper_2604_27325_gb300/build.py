@@ -19,6 +19,9 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["bed_api.cu", "bed_kernel_16.cu", "bed_kernel_32.cu", "bed_kernel_48.cu", "bed_kernel_64.cu", "bed_ragged.cu",
            "bed_backward.cu", "bed_serve.cu", "bed_peak.cu"]
 HEADERS = ["bed_internal.h", "bed_kernel.cuh"]
+# exports only the C ABI (bed_*): every other symbol, the per-kernel attribute flags included, stays
+# local, so that two copies of the library in one process keep separate state
+VERSION_SCRIPT = os.path.join(CSRC, "bed.map")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -60,9 +63,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(jobs) or 1) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
+    if force or jobs or _stale(LIB, objs + [VERSION_SCRIPT]):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([cc, *ARCH, "-shared", "-o", tmp, *objs])
+        run([cc, *ARCH, "-shared", "-Xlinker", "--version-script=" + VERSION_SCRIPT, "-o", tmp, *objs])
         os.replace(tmp, LIB)
     return LIB
 
