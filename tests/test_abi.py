@@ -29,6 +29,23 @@ def test_library_exports_every_declared_symbol():
     assert sorted(B.EXPORTED) == names
 
 
+def test_library_exports_only_the_declared_functions():
+    """The dynamic symbol table holds exactly the functions of include/bed.h: everything else (kernel
+    stubs, template instantiations and their function-local statics) is local to the library."""
+    import shutil
+    import subprocess
+
+    from paper_2604_27325_gb300 import build
+
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm is not installed")
+    B.lib()
+    out = subprocess.run([nm, "-D", "--defined-only", build.LIB], capture_output=True, text=True, check=True).stdout
+    names = sorted(line.split()[-1] for line in out.splitlines() if line.strip())
+    assert names == declared_functions()
+
+
 def test_constants_and_strings():
     assert B.bed_max_n() == 64
     assert B.bed_status_string(B.BED_OK) == "BED_OK"
