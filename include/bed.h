@@ -95,6 +95,10 @@ typedef struct {
                                 in 1..2^20: ceil(batch / k) blocks, block i solving matrices i, i + blocks,
                                 ... in turn (about k each) in its shared memory. Results are bitwise the same
                                 whatever k; the ragged kernel and the server hand out their own units. */
+    int n_bisect_first;      /* bisection steps per secular root (Eq. (13)-(15)) before the multi-section
+                                steps of Eq. (16), 1..64 (default 1, the paper's single bisection); the
+                                steps after the first count toward max_section_iters, and the switch to
+                                Halley (Eq. (17)) may come before they are all taken */
 } bed_params;
 
 /* Fills *p with the defaults listed above. */

@@ -43,6 +43,7 @@ class bed_params(C.Structure):
         ("merge_tensor_cores", C.c_int),
         ("stage_wait_us", C.c_int),
         ("matrices_per_cta", C.c_int),
+        ("n_bisect_first", C.c_int),
     ]
 
 

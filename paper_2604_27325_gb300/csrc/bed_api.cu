@@ -151,6 +151,7 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
     if (prm->merge_tensor_cores != 0 && prm->merge_tensor_cores != 1) return false;
     if (prm->stage_wait_us < 0 || prm->stage_wait_us > 60000000) return false;
     if (prm->matrices_per_cta < 0 || prm->matrices_per_cta > (1 << 20)) return false;
+    if (prm->n_bisect_first < 1 || prm->n_bisect_first > 64) return false;
     kp->k_ms = prm->k_multisection;
     kp->max_sec = prm->max_section_iters;
     kp->max_halley = prm->max_halley_iters;
@@ -159,6 +160,7 @@ bool make_kparams(const bed_params* p, bed_params* prm, KParams* kp)
     kp->defl_c = prm->deflation_tol_scale;
     kp->retire = prm->retire_by_vote;
     kp->merge_tc = prm->merge_tensor_cores;
+    kp->n_bisect = prm->n_bisect_first;
     kp->stage_wait_ns = 1000ull * static_cast<unsigned long long>(prm->stage_wait_us);
     return true;
 }
@@ -302,6 +304,7 @@ void bed_default_params(bed_params* p)
     p->merge_tensor_cores = 0;
     p->stage_wait_us = 2000000;
     p->matrices_per_cta = 0;
+    p->n_bisect_first = 1;
 }
 
 bed_status bed_eigh_f32(const float* A, float* W, float* V, int32_t* info, int64_t batch, int n,

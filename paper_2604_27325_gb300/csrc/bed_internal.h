@@ -39,6 +39,7 @@ struct KParams {
     float defl_c;     // deflation tolerance scale
     int retire;       // warp-vote retirement of converged roots
     int merge_tc;     // merge products on the tensor cores (split-3xTF32)
+    int n_bisect;     // bisection steps before the multi-section of Eq. (16), >= 1
     unsigned long long stage_wait_ns;  // limit of the wait for a matrix's staging copy
 };
 

@@ -554,7 +554,8 @@ __device__ __forceinline__ RootOut secular_root(const float2* __restrict__ dz, i
                     }
                     h = hn;
                 } else {
-                    h = fmaf(U - L, kinv, L);  // Eq. (16)
+                    // Eq. (16); the first n_bisect - 1 of these steps bisect (Eq. (13)-(15))
+                    h = fmaf(U - L, (nsec + 1 < kp.n_bisect) ? 0.5f : kinv, L);
                 }
             }
         } else {

@@ -54,7 +54,7 @@ def test_constants_and_strings():
     assert C.sizeof(B.bed_counters) == 32
     p = B.bed_default_params()
     assert (p.leaf_size, p.k_multisection, p.retire_by_vote, p.threads_per_matrix) == (0, 4, 1, 0)
-    assert p.merge_tensor_cores == 0 and p.matrices_per_cta == 0
+    assert p.merge_tensor_cores == 0 and p.matrices_per_cta == 0 and p.n_bisect_first == 1
     assert p.section_rel_eps == 2.0**-1
 
 
@@ -87,7 +87,7 @@ def test_empty_batch_is_ok_without_launch():
      ("max_section_iters", -1), ("section_rel_eps", 0.0), ("section_rel_eps", 1.0), ("stop_c", 0.5),
      ("deflation_tol_scale", 0.0), ("retire_by_vote", 2), ("threads_per_matrix", 100),
      ("merge_tensor_cores", 2), ("merge_tensor_cores", -1), ("matrices_per_cta", -1),
-     ("matrices_per_cta", (1 << 20) + 1)],
+     ("matrices_per_cta", (1 << 20) + 1), ("n_bisect_first", 0), ("n_bisect_first", 65)],
 )
 def test_bad_params(field, value):
     p = B.make_params(**{field: value})

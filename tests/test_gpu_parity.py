@@ -141,7 +141,8 @@ def test_vote_retirement_is_result_neutral(n):
 @pytest.mark.parametrize(
     "kw",
     [dict(leaf_size=1), dict(k_multisection=2), dict(k_multisection=8, section_rel_eps=2.0**-10),
-     dict(section_rel_eps=0.5, max_section_iters=0), dict(threads_per_matrix=128)],
+     dict(section_rel_eps=0.5, max_section_iters=0), dict(threads_per_matrix=128), dict(n_bisect_first=3),
+     dict(n_bisect_first=8, section_rel_eps=2.0**-10)],
 )
 def test_parameter_variants_hold_tolerance(kw):
     A = wl.covariance(32, 64 if kw.get("threads_per_matrix") == 128 else 40, seed=31)
@@ -166,6 +167,28 @@ def test_counters():
     total = 16 * sum(hi - lo for lo, _, hi, _ in B.bed_plan_describe(32, B.make_params().leaf_size))
     assert roots + deflated == total
     assert roots > 0 and evals > roots
+
+
+def test_bisection_steps_reach_the_secular_solver():
+    """n_bisect_first changes the sectioning points (bisection instead of Eq. (16)'s multi-section), so
+    with a small switch threshold the f evaluations the roots take change, while the results stay within
+    tolerance (checked in test_parameter_variants_hold_tolerance)."""
+    A = wl.covariance(16, 32, seed=43)
+    Ad = torch.from_numpy(A).cuda()
+    W = torch.empty(16, 32, device="cuda")
+    V = torch.empty(16, 32, 32, device="cuda")
+    evals = {}
+    for nb in (1, 6):
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        p = B.make_params(n_bisect_first=nb, section_rel_eps=2.0**-10)
+        st = B.bed_eigh_f32_counted(Ad.data_ptr(), W.data_ptr(), V.data_ptr(), None, 16, 32, p, cnt.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
+        assert st == B.BED_OK
+        torch.cuda.synchronize()
+        matrices, roots, ev, _ = cnt.tolist()
+        assert matrices == 16 and roots > 0
+        evals[nb] = ev
+    assert evals[1] != evals[6]
 
 
 def test_host_buffers_end_to_end():
