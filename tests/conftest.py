@@ -13,7 +13,7 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # GPU tests are skipped, not failed, where no GPU is present; the driver selects them with -m gpu.
+    # GPU tests are skipped, not failed, where no GPU is present; `-m gpu` selects them.
     try:
         import torch
 
